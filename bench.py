@@ -1,0 +1,509 @@
+#!/usr/bin/env python3
+"""Benchmark of the batched level-wise B+ tree point search on GB300.
+
+Workload (default): one static tree of 2^24 distinct uniform uint64 keys,
+fanout 32, uint64 rank values; batches of 2^20 point lookups at 90% hits
+(uniform).  One step = one pass of the whole search path over one batch:
+the on-device radix sort of the batch, then the level-wise descent, leaf
+probe and scatter to input order.  Inputs are resident in HBM when a step
+starts; L2 is flushed (a 256 MB device write) before every timed step.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the CPU oracle
+(the plain pointer B+ tree searched one query at a time) on the host cores
+instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2604_21117_gb300 import workloads as W  # noqa: E402
+
+METRIC = "batched B+tree lookups/s at 2^24 keys, learned vs plain; p99 µs; HBM GB/s"
+UNIT = "lookups/s"
+L2_FLUSH_BYTES = 256 << 20
+
+# DRAM bytes of one descent launch on the default workload, from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum), valid only while
+# the kernel source is the one captured (sha256 prefix of csrc/search.cu).
+NCU_DESCEND_TRAFFIC = {"search_cu_sha256": None, "bytes_per_launch": None}
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--keys", type=int, default=1 << 24)
+    p.add_argument("--batch", type=int, default=1 << 20)
+    p.add_argument("--fanout", type=int, default=32)
+    p.add_argument("--hit", type=float, default=0.9)
+    p.add_argument("--zipf", type=float, default=None)
+    p.add_argument("--sort-bits", type=int, default=-1)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-extras", action="store_true", help="skip e2e / small-batch latency legs")
+    return p.parse_args(argv)
+
+
+# ------------------------------------------------------------ workload
+
+def workload_name(a) -> str:
+    dist = "uniform" if a.zipf is None else f"Zipf(s={a.zipf})"
+    return (f"plain level-wise search: {a.keys} distinct uniform uint64 keys, fanout {a.fanout}, "
+            f"uint64 values, batch {a.batch}, {int(round(a.hit * 100))}% hits, {dist} queries")
+
+
+def make_tree_data(a):
+    keys = W.uniform_keys(a.keys, 64, seed=W.SEED_BASE + 2)
+    vals = W.rank_values(a.keys, 64)
+    return keys, vals
+
+
+def make_batches(a, keys, count: int, rank: int = 0):
+    return [W.make_queries(keys, a.batch, a.hit, seed=W.SEED_BASE + 2 + 1000 * (i + 1) + 7919 * rank,
+                           width_bits=64, zipf_s=a.zipf) for i in range(count)]
+
+
+def level_node_max(keys: np.ndarray, level_nodes: list[int]) -> list[np.ndarray]:
+    """Largest key under every node of every level (root first), from the
+    sorted keys and the level sizes of the even bulk load."""
+    n = keys.size
+    L = level_nodes[-1]
+    base, rem = divmod(n, L)
+    i = np.arange(L, dtype=np.int64)
+    ends = (i + 1) * base + np.minimum(i + 1, rem)
+    node_max = keys[ends - 1]
+    out = [node_max]
+    for l in range(len(level_nodes) - 2, -1, -1):
+        N, C = level_nodes[l], level_nodes[l + 1]
+        b, r = divmod(C, N)
+        j = np.arange(N, dtype=np.int64)
+        node_max = node_max[(j + 1) * b + np.minimum(j + 1, r) - 1]
+        out.insert(0, node_max)
+    return out
+
+
+def touched(keys: np.ndarray, level_nodes: list[int], m: int, q: np.ndarray, val_bytes: int = 8):
+    """Distinct nodes per level on the batch's root-to-leaf paths and
+    distinct 32-byte leaf-value sectors its hits read."""
+    q = q.astype(np.uint64)
+    maxes = level_node_max(keys, level_nodes)
+    counts = []
+    leaf = None
+    for l, mx in enumerate(maxes):
+        idx = np.minimum(np.searchsorted(mx, q, side="left"), level_nodes[l] - 1)
+        counts.append(int(np.unique(idx).size))
+        leaf = idx
+    n = keys.size
+    L = level_nodes[-1]
+    base, rem = divmod(n, L)
+    first = leaf * base + np.minimum(leaf, rem)
+    rank = np.searchsorted(keys, q, side="left")
+    inb = rank < n
+    hit = np.zeros(q.size, bool)
+    hit[inb] = keys[rank[inb]] == q[inb]
+    slot = rank[hit] - first[hit]
+    sectors = np.unique(((leaf[hit] * m + slot) * val_bytes) // 32).size
+    return counts, int(sectors)
+
+
+def descend_algorithmic_bytes(counts, sectors, m, kb, vb, B) -> int:
+    """Bytes the descent must move at least: every distinct node's key block
+    once, every distinct value sector once, the sorted queries and their
+    positions in, the values and found flags out."""
+    return sum(counts) * m * kb + sectors * 32 + B * (kb + 4) + B * (vb + 1)
+
+
+# ------------------------------------------------------------- helpers
+
+def iqm(x) -> float:
+    """Interquartile mean: the mean of the middle half of the sorted samples
+    (the paper's Eq. 2 reports this statistic)."""
+    s = sorted(x)
+    n = len(s)
+    lo, hi = n // 4, n - n // 4
+    mid = s[lo:hi] if hi > lo else s
+    return float(sum(mid) / len(mid))
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 100 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append((time.time(), parts))
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(p[1]) for _, p in self.samples if num(p[1]) is not None]
+        mx = [num(p[2]) for _, p in self.samples if num(p[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for _, p in self.samples:
+            for nm, v in zip(names, p[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+def src_sha256() -> str:
+    with open(os.path.join(ROOT, "paper_2604_21117_gb300", "csrc", "search.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+# ------------------------------------------------------------ dist
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def dist_init(world: int, backend: str):
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist
+
+
+def reduce_max(x: float, world: int, device=None) -> float:
+    """Max of a float over the ranks (identity at world size 1)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------- CPU oracle
+
+def cpu_baseline(keys, vals, m, q, budget_s: float = 12.0):
+    """Time the CPU oracle (pointer B+ tree, one query at a time) on a
+    bounded sample of the batch: single thread and all host cores."""
+    import oracle
+    t0 = time.perf_counter()
+    tree = oracle.OracleTree(keys, vals, m)
+    build_s = time.perf_counter() - t0
+    cores = os.cpu_count() or 1
+    probe = q[: min(q.size, 1 << 14)]
+    t0 = time.perf_counter()
+    tree.search(probe)
+    per_q = (time.perf_counter() - t0) / probe.size
+    n1 = int(min(q.size, max(1 << 14, (budget_s * 0.4) / max(per_q, 1e-9))))
+    t0 = time.perf_counter()
+    tree.search_mt(q[:n1], 1)
+    t1 = time.perf_counter() - t0
+    nm = int(min(q.size, max(1 << 16, (budget_s * 0.4) * cores / max(per_q, 1e-9))))
+    reps = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        tree.search_mt(q[:nm], cores)
+        reps.append(time.perf_counter() - t0)
+    tm = iqm(reps)
+    tree.close()
+    return {"value": nm / tm, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "value_1thread": n1 / t1,
+            "sample": (f"first {nm} queries of one batch on {cores} threads (batch split evenly), "
+                       f"IQM of 3 runs; 1-thread figure on the first {n1}; oracle tree build "
+                       f"{build_s:.1f} s untimed")}
+
+
+# ---------------------------------------------------------- our arm
+
+def run_ours(a):
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist_init(world, "nccl")
+    from paper_2604_21117_gb300 import build_lib
+    build_lib.build()
+    from paper_2604_21117_gb300 import btree as bt
+
+    keys, vals = make_tree_data(a)
+    pool = 4
+    batches = make_batches(a, keys, pool, rank)
+    tree = bt.BTree(keys, vals, a.fanout)
+    m, kb, vb, B = a.fanout, 8, 8, a.batch
+
+    alg = []
+    for qb in batches:
+        counts, sectors = touched(keys, tree.level_nodes, m, qb)
+        alg.append((counts, sectors, descend_algorithmic_bytes(counts, sectors, m, kb, vb, B)))
+
+    dq = [torch.from_numpy(qb).cuda() for qb in batches]
+    sq = torch.empty(B, dtype=torch.uint64, device="cuda")
+    si = torch.empty(B, dtype=torch.int32, device="cuda")
+    out_v = torch.empty(B, dtype=torch.uint64, device="cuda")
+    out_f = torch.empty(B, dtype=torch.uint8, device="cuda")
+    nb = tree.workspace_bytes(B)
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    sort_bits = a.sort_bits
+
+    def step(i):
+        x = dq[i % pool]
+        bt.bt_sort_batch(tree.handle, x, B, sort_bits, sq, si, ws, nb, stream)
+        bt.bt_descend_sorted(tree.handle, sq, si, B, out_v, out_f, None, stream)
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    for i in range(a.warmup):
+        flush.fill_(i)
+        step(i)
+    torch.cuda.synchronize()
+
+    K = a.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    barrier(world)
+    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    for i in range(K):
+        flush.fill_(i)
+        e0, e1, e2 = ev[i]
+        x = dq[i % pool]
+        e0.record(stream)
+        bt.bt_sort_batch(tree.handle, x, B, sort_bits, sq, si, ws, nb, stream)
+        e1.record(stream)
+        bt.bt_descend_sorted(tree.handle, sq, si, B, out_v, out_f, None, stream)
+        e2.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    wall = time.perf_counter() - t_wall0
+    step_ms = [e[0].elapsed_time(e[2]) for e in ev]
+    desc_ms = [e[1].elapsed_time(e[2]) for e in ev]
+    sort_ms = [e[0].elapsed_time(e[1]) for e in ev]
+    total_s = sum(step_ms) / 1e3
+    total_s_max = reduce_max(total_s, world, device="cuda")
+    value = B * K * world / total_s_max
+
+    # correctness spot check of the last step against the plain definition
+    last = batches[(K - 1) % pool]
+    got_v = out_v.cpu().numpy()
+    got_f = out_f.cpu().numpy()
+    pos = np.searchsorted(keys, last)
+    hit = (pos < keys.size) & (keys[np.minimum(pos, keys.size - 1)] == last)
+    ok = bool(np.array_equal(got_f.astype(bool), hit) and np.array_equal(got_v[hit], vals[pos[hit]]))
+
+    # bytes and roofline of the dominant kernel (the descent)
+    desc_bytes = [alg[i % pool][2] for i in range(K)]
+    node_bytes = [sum(alg[i % pool][0]) * m * kb + alg[i % pool][1] * 32 for i in range(K)]
+    achieved = statistics.fmean(desc_bytes) / (statistics.fmean(desc_ms) / 1e3) / 1e9
+    peak, peak_kind = measured_peaks()
+    traffic = None
+    if NCU_DESCEND_TRAFFIC["search_cu_sha256"] == src_sha256():
+        traffic = NCU_DESCEND_TRAFFIC["bytes_per_launch"]
+    step_gbs = statistics.fmean(node_bytes) / (statistics.fmean(step_ms) / 1e3) / 1e9
+    passes = bt.bt_sort_passes(tree.handle, B, sort_bits)
+    # our kernels per step: radix histogram + scan + one scatter per pass (or
+    # one copy kernel when the sort is skipped), then the descent
+    launches_per_step = (2 + passes if passes else 1) + 1
+    sdev = sorted(step_ms)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": a.warmup, "ms_per_step": statistics.fmean(step_ms), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic (seeded uniform keys and query mix)",
+        "config": {"workload": workload_name(a), "keys": a.keys, "fanout": m, "batch": B,
+                   "hit_frac": a.hit, "query_dist": "uniform" if a.zipf is None else f"zipf{a.zipf}",
+                   "sort_bits": "auto" if sort_bits < 0 else sort_bits,
+                   "l2": "flushed before every timed step (256 MB device write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "p50_us": 1e3 * sdev[len(sdev) // 2], "p99_us": 1e3 * sdev[min(len(sdev) - 1, int(0.99 * len(sdev)))],
+        "iqm_us": 1e3 * iqm(step_ms),
+        "phase_ms": {"sort": statistics.fmean(sort_ms), "descend": statistics.fmean(desc_ms)},
+        "hbm_gbs": step_gbs,
+        "roofline": {"kernel": "k_descend (level-wise descent + leaf probe + scatter)", "bound": "hbm",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_kind": f"{peak_kind} (hbm_gbs)", "traffic": traffic,
+                     "algorithmic_bytes_per_launch": statistics.fmean(desc_bytes),
+                     "distinct_nodes_per_level": alg[0][0], "distinct_value_sectors": alg[0][1]},
+        "gpu_launches": launches_per_step * K,
+        "correct_last_step": ok, "wall_s_timed_loop": wall,
+    }
+
+    if not a.no_extras:
+        # end to end through the host-buffer entry point: H2D of the queries,
+        # search, D2H of values and found flags, every step
+        hq = torch.from_numpy(batches[0]).pin_memory()
+        hv = torch.empty(B, dtype=torch.uint64).pin_memory()
+        hf = torch.empty(B, dtype=torch.uint8).pin_memory()
+        nbh = bt.bt_search_host_workspace_bytes(tree.handle, B)
+        wsh = torch.empty(nbh, dtype=torch.uint8, device="cuda")
+        for _ in range(3):
+            bt.bt_search_batch_host(tree.handle, hq, B, hv, hf, wsh, nbh, stream)
+        torch.cuda.synchronize()
+        Ke = max(10, min(K, 200))
+        tt = []
+        for i in range(Ke):
+            flush.fill_(i)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            bt.bt_search_batch_host(tree.handle, hq, B, hv, hf, wsh, nbh, stream)
+            e1.record(stream)
+            e1.synchronize()
+            tt.append(e0.elapsed_time(e1))
+        e2e_s = reduce_max(sum(tt) / 1e3, world, device="cuda")
+        line["e2e"] = {"value": B * Ke * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": B * kb,
+                       "d2h_bytes_per_step": B * (vb + 1), "steps": Ke,
+                       "entry_point": "bt_search_batch_host (pinned host buffers)"}
+        # small-batch latency (the paper's batch sizes go to 1000)
+        lat = {}
+        for b in (1, 1024):
+            qs = torch.from_numpy(batches[1][:b].copy()).cuda()
+            v1 = torch.empty(b, dtype=torch.uint64, device="cuda")
+            f1 = torch.empty(b, dtype=torch.uint8, device="cuda")
+            n1 = tree.workspace_bytes(b)
+            w1 = torch.empty(max(n1, 1), dtype=torch.uint8, device="cuda")
+            for _ in range(20):
+                bt.bt_search_batch(tree.handle, qs, b, v1, f1, w1, n1, stream)
+            ts = []
+            for i in range(500):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                bt.bt_search_batch(tree.handle, qs, b, v1, f1, w1, n1, stream)
+                e1.record(stream)
+                ts.append((e0, e1))
+            torch.cuda.synchronize()
+            us = sorted(1e3 * x.elapsed_time(y) for x, y in ts)
+            lat[f"b{b}"] = {"p50_us": us[len(us) // 2], "p99_us": us[int(0.99 * len(us))],
+                            "lookups_per_s": b / (statistics.fmean(us) / 1e6)}
+        line["small_batch_latency"] = lat
+
+    sampler.stop()
+    line["clocks"] = sampler.summary()
+
+    if rank == 0 and not a.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(keys, vals, m, batches[0])
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    tree.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------ reference arm
+
+def run_reference(a):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    keys, vals = make_tree_data(a)
+    q = make_batches(a, keys, 1)[0]
+    tree = oracle.OracleTree(keys, vals, a.fanout)
+    cores = os.cpu_count() or 1
+    sample = min(q.size, 1 << 16)
+    qs = q[:sample]
+    for _ in range(a.warmup):
+        tree.search_mt(qs, cores)
+    ts = []
+    for _ in range(a.steps):
+        t0 = time.perf_counter()
+        tree.search_mt(qs, cores)
+        ts.append(time.perf_counter() - t0)
+    total = sum(ts)
+    value = sample * a.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * total / a.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic (seeded uniform keys and query mix)",
+        "config": {"workload": workload_name(a), "keys": a.keys, "fanout": a.fanout, "batch": a.batch,
+                   "hit_frac": a.hit, "query_dist": "uniform" if a.zipf is None else f"zipf{a.zipf}"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"each step: the first {sample} queries of the batch, split evenly "
+                                   f"over {cores} threads"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    tree.close()
+    print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    a = parse_args(argv)
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

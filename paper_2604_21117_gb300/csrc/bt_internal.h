@@ -1,0 +1,43 @@
+// Internal definitions shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "btree_gb300.h"
+
+namespace btgb {
+
+// Device-side description of a built tree, passed to kernels by value.
+//
+// Nodes of level l are numbered 0..nodes[l]-1 left to right.  The even bulk
+// load makes the shape arithmetic: inner node i of level l owns children
+// first_child(l, i) .. first_child(l, i) + span(l, i) - 1 of level l+1, with
+// span(l, i) = cbase[l] + (i < crem[l]) and
+// first_child(l, i) = i * cbase[l] + min(i, crem[l]).  For the leaf level the
+// same two numbers split the n keys over the leaves, so leaf i holds
+// cbase + (i < crem) keys.  No child pointers are stored (Sec. IV-B embeds
+// child addresses in each node; here they follow from the node's index).
+struct DevTree {
+    const void *keys[BT_MAX_LEVELS];   // level key blocks, m slots per node
+    uint64_t nodes[BT_MAX_LEVELS];
+    uint64_t cbase[BT_MAX_LEVELS];
+    uint64_t crem[BT_MAX_LEVELS];
+    const void *vals;                  // leaf value blocks, m slots per leaf
+    uint64_t kmin, kmax;               // smallest and largest key (sort normalisation)
+    int height;
+    int m;
+    int key_bytes, val_bytes;
+};
+
+}  // namespace btgb
+
+struct bt_tree {
+    btgb::DevTree dev;
+    bt_info info;
+    void *d_image;
+};
+
+namespace btgb {
+void set_error_detail(const char *what, cudaError_t err);
+}

@@ -1,0 +1,235 @@
+// Host-side tree construction and bookkeeping (bt_build, bt_free, bt_tree_info).
+//
+// The tree is built once on the host and copied to device memory once
+// (Sec. IV-B's BFS "mapper" flattens a pointer tree into a uniform node
+// array; Sec. V-B treats that as one-time initialisation).  Here the levels
+// are written directly in structure-of-arrays form from the sorted keys.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "bt_internal.h"
+
+namespace btgb {
+
+static thread_local char g_detail[256] = "";
+
+void set_error_detail(const char *what, cudaError_t err)
+{
+    snprintf(g_detail, sizeof(g_detail), "%s: %s", what, cudaGetErrorString(err));
+}
+
+static inline uint64_t load_uint(const void *p, uint64_t i, int bytes)
+{
+    return bytes == 8 ? static_cast<const uint64_t *>(p)[i] : static_cast<const uint32_t *>(p)[i];
+}
+
+static inline void store_uint(void *p, uint64_t i, int bytes, uint64_t v)
+{
+    if (bytes == 8)
+        static_cast<uint64_t *>(p)[i] = v;
+    else
+        static_cast<uint32_t *>(p)[i] = static_cast<uint32_t>(v);
+}
+
+static inline uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace btgb
+
+using namespace btgb;
+
+extern "C" const char *bt_last_error_detail(void) { return g_detail; }
+
+extern "C" const char *bt_status_str(bt_status s)
+{
+    switch (s) {
+    case BT_OK: return "ok";
+    case BT_ERR_ARG: return "invalid argument";
+    case BT_ERR_UNSORTED: return "build keys are not in ascending order";
+    case BT_ERR_DUPLICATE: return "build keys contain a duplicate";
+    case BT_ERR_FANOUT: return "fanout must be 8, 16, 32 or 64";
+    case BT_ERR_NOMEM: return "out of memory";
+    case BT_ERR_CUDA: return "CUDA runtime error";
+    case BT_ERR_TIMEOUT: return "bounded device wait timed out";
+    case BT_ERR_WORKSPACE: return "workspace missing or too small";
+    }
+    return "unknown status";
+}
+
+extern "C" bt_status bt_build(const void *h_keys, const void *h_vals, uint64_t n, bt_width key_w,
+                              bt_width val_w, uint32_t fanout, bt_stream stream, bt_tree **out)
+{
+    if (!out) return BT_ERR_ARG;
+    if ((key_w != BT_U32 && key_w != BT_U64) || (val_w != BT_U32 && val_w != BT_U64))
+        return BT_ERR_ARG;
+    if (fanout != 8 && fanout != 16 && fanout != 32 && fanout != 64) return BT_ERR_FANOUT;
+    if (n > 0 && (!h_keys || !h_vals)) return BT_ERR_ARG;
+    const int kb = static_cast<int>(key_w), vb = static_cast<int>(val_w);
+    const uint64_t m = fanout, kmax_per_node = m - 1;
+
+    for (uint64_t i = 1; i < n; ++i) {
+        uint64_t a = load_uint(h_keys, i - 1, kb), b = load_uint(h_keys, i, kb);
+        if (b < a) return BT_ERR_UNSORTED;
+        if (b == a) return BT_ERR_DUPLICATE;
+    }
+
+    // Level sizes, leaves first.
+    std::vector<uint64_t> up;  // up[0] = leaves, up[k] = k levels above
+    if (n > 0) {
+        uint64_t c = (n + kmax_per_node - 1) / kmax_per_node;
+        up.push_back(c);
+        while (c > 1) {
+            c = (c + m - 1) / m;
+            up.push_back(c);
+        }
+    }
+    const int h = static_cast<int>(up.size());
+    if (h > BT_MAX_LEVELS) return BT_ERR_ARG;
+    for (uint64_t c : up)
+        if (c >= (1ull << 32)) return BT_ERR_ARG;
+
+    bt_tree *t = new (std::nothrow) bt_tree;
+    if (!t) return BT_ERR_NOMEM;
+    memset(t, 0, sizeof(*t));
+    DevTree &d = t->dev;
+    d.height = h;
+    d.m = static_cast<int>(m);
+    d.key_bytes = kb;
+    d.val_bytes = vb;
+    t->info.height = static_cast<uint32_t>(h);
+    t->info.fanout = fanout;
+    t->info.key_bytes = static_cast<uint32_t>(kb);
+    t->info.val_bytes = static_cast<uint32_t>(vb);
+    t->info.n = n;
+    if (n > 0) {
+        d.kmin = load_uint(h_keys, 0, kb);
+        d.kmax = load_uint(h_keys, n - 1, kb);
+    }
+
+    // Byte layout: level key arrays root first, then leaf values.
+    uint64_t off = 0;
+    for (int l = 0; l < h; ++l) {
+        const uint64_t N = up[h - 1 - l];
+        d.nodes[l] = N;
+        t->info.level_nodes[l] = N;
+        t->info.level_key_offset[l] = off;
+        off = align_up(off + N * m * kb, 256);
+    }
+    t->info.leaf_val_offset = off;
+    if (h > 0) off = align_up(off + up[0] * m * vb, 256);
+    t->info.device_bytes = off;
+
+    // Shape arithmetic: children (or keys, for leaves) per node.
+    for (int l = 0; l < h; ++l) {
+        const uint64_t N = d.nodes[l];
+        const uint64_t below = (l + 1 < h) ? d.nodes[l + 1] : n;
+        d.cbase[l] = below / N;
+        d.crem[l] = below % N;
+    }
+
+    if (off == 0) {  // empty tree: nothing on the device
+        *out = t;
+        return BT_OK;
+    }
+
+    unsigned char *img = static_cast<unsigned char *>(malloc(off));
+    if (!img) {
+        delete t;
+        return BT_ERR_NOMEM;
+    }
+    memset(img, 0, off);
+
+    // Leaves: keys and values, padding key slots with all-ones.
+    const int leaf = h - 1;
+    const uint64_t L = d.nodes[leaf];
+    void *lk = img + t->info.level_key_offset[leaf];
+    void *lv = img + t->info.leaf_val_offset;
+    const uint64_t pad = (kb == 8) ? ~0ull : 0xFFFFFFFFull;
+    std::vector<uint64_t> node_max(L);
+    {
+        uint64_t first = 0;
+        for (uint64_t i = 0; i < L; ++i) {
+            const uint64_t cnt = d.cbase[leaf] + (i < d.crem[leaf] ? 1 : 0);
+            for (uint64_t j = 0; j < m; ++j) {
+                if (j < cnt) {
+                    store_uint(lk, i * m + j, kb, load_uint(h_keys, first + j, kb));
+                    store_uint(lv, i * m + j, vb, load_uint(h_vals, first + j, vb));
+                } else {
+                    store_uint(lk, i * m + j, kb, pad);
+                }
+            }
+            node_max[i] = load_uint(h_keys, first + cnt - 1, kb);
+            first += cnt;
+        }
+    }
+    // Inner levels bottom-up: separator j = largest key under child j.
+    for (int l = leaf - 1; l >= 0; --l) {
+        const uint64_t N = d.nodes[l];
+        void *ik = img + t->info.level_key_offset[l];
+        std::vector<uint64_t> upper_max(N);
+        uint64_t first = 0;
+        for (uint64_t i = 0; i < N; ++i) {
+            const uint64_t span = d.cbase[l] + (i < d.crem[l] ? 1 : 0);
+            for (uint64_t j = 0; j < m; ++j)
+                store_uint(ik, i * m + j, kb, (j + 1 < span) ? node_max[first + j] : pad);
+            upper_max[i] = node_max[first + span - 1];
+            first += span;
+        }
+        node_max.swap(upper_max);
+    }
+
+    cudaError_t e = cudaMalloc(&t->d_image, off);
+    if (e != cudaSuccess) {
+        set_error_detail("cudaMalloc(tree image)", e);
+        free(img);
+        delete t;
+        return e == cudaErrorMemoryAllocation ? BT_ERR_NOMEM : BT_ERR_CUDA;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    e = cudaMemcpyAsync(t->d_image, img, off, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    free(img);
+    if (e != cudaSuccess) {
+        set_error_detail("copy of tree image to device", e);
+        cudaFree(t->d_image);
+        delete t;
+        return BT_ERR_CUDA;
+    }
+    for (int l = 0; l < h; ++l)
+        d.keys[l] = static_cast<unsigned char *>(t->d_image) + t->info.level_key_offset[l];
+    d.vals = static_cast<unsigned char *>(t->d_image) + t->info.leaf_val_offset;
+    t->info.d_image = t->d_image;
+    *out = t;
+    return BT_OK;
+}
+
+extern "C" void bt_free(bt_tree *t)
+{
+    if (!t) return;
+    if (t->d_image) cudaFree(t->d_image);
+    delete t;
+}
+
+extern "C" bt_status bt_tree_info(const bt_tree *t, bt_info *out)
+{
+    if (!t || !out) return BT_ERR_ARG;
+    *out = t->info;
+    return BT_OK;
+}
+
+extern "C" bt_status bt_tree_copy_image(const bt_tree *t, void *h_dst, uint64_t bytes)
+{
+    if (!t || (!h_dst && bytes)) return BT_ERR_ARG;
+    if (bytes > t->info.device_bytes) return BT_ERR_ARG;
+    if (bytes == 0) return BT_OK;
+    cudaError_t e = cudaMemcpy(h_dst, t->d_image, bytes, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        set_error_detail("copy of tree image to host", e);
+        return BT_ERR_CUDA;
+    }
+    return BT_OK;
+}

@@ -1,0 +1,95 @@
+"""The C-ABI library loads, exports every declared symbol, and its host-side
+argument checks work without a GPU (no compute call is made here)."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bt():
+    from paper_2604_21117_gb300 import build_lib
+    build_lib.build()
+    from paper_2604_21117_gb300 import btree
+    return btree
+
+
+def _declared_functions():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if f.endswith(".h"):
+            text = open(os.path.join(inc, f)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(bt_[a-z_0-9]+)\s*\(", text))
+    return names
+
+
+def test_every_declared_symbol_is_exported(bt):
+    declared = _declared_functions()
+    assert declared, "no declarations found"
+    lib = ctypes.CDLL(bt.LIB_PATH)
+    for name in declared:
+        assert hasattr(lib, name), f"{name} declared in include/ but not exported"
+    assert declared == set(bt.EXPORTED)
+
+
+def test_status_strings(bt):
+    for code in range(9):
+        assert bt.bt_status_str(code)
+    assert bt.bt_status_str(0) == "ok"
+
+
+def test_build_rejects_bad_arguments_before_touching_the_gpu(bt):
+    k = np.array([1, 2, 3], np.uint64)
+    with pytest.raises(bt.BTreeError) as e:
+        bt.bt_build(k, k, 12, stream=0)
+    assert e.value.code == "BT_ERR_FANOUT"
+    with pytest.raises(bt.BTreeError) as e:
+        bt.bt_build(np.array([1, 3, 2], np.uint64), k, 16, stream=0)
+    assert e.value.code == "BT_ERR_UNSORTED"
+    with pytest.raises(bt.BTreeError) as e:
+        bt.bt_build(np.array([1, 3, 3], np.uint64), k, 16, stream=0)
+    assert e.value.code == "BT_ERR_DUPLICATE"
+    with pytest.raises(ValueError):
+        bt.bt_build(np.array([1, 2], np.int64), np.array([1, 2], np.int64), 16, stream=0)
+
+
+def test_empty_tree_needs_no_device_memory(bt):
+    h = bt.bt_build(np.empty(0, np.uint64), np.empty(0, np.uint64), 32, stream=0)
+    info = bt.bt_tree_info(h)
+    assert info.height == 0 and info.n == 0 and info.device_bytes == 0
+    # nq = 0 is a no-op that succeeds without a device
+    bt.bt_search_batch(h, 0, 0, 0, 0, 0, 0, stream=0)
+    bt.bt_free(h)
+
+
+def test_workspace_size_is_monotone_and_aligned(bt):
+    h = bt.bt_build(np.empty(0, np.uint32), np.empty(0, np.uint32), 16, stream=0)
+    prev = 0
+    for nq in (1, 31, 32, 1000, 4096, 4097, 1 << 20):
+        w = bt.bt_search_workspace_bytes(h, nq)
+        assert w >= prev and w % 256 == 0 and w >= 2 * nq * (4 + 4)
+        prev = w
+    assert bt.bt_search_workspace_bytes(h, 0) == 0
+    bt.bt_free(h)
+
+
+def test_search_argument_errors(bt):
+    h = bt.bt_build(np.empty(0, np.uint64), np.empty(0, np.uint64), 32, stream=0)
+    with pytest.raises(bt.BTreeError) as e:
+        bt.bt_search_batch(h, 0, 10, 0, 0, 0, 0, stream=0)  # null pointers
+    assert e.value.code == "BT_ERR_ARG"
+    with pytest.raises(bt.BTreeError) as e:
+        bt.bt_search_batch(h, 256, 10, 512, 768, 0, 0, stream=0)  # no workspace
+    assert e.value.code == "BT_ERR_WORKSPACE"
+    with pytest.raises(bt.BTreeError) as e:
+        bt.bt_search_batch(h, 256, 1 << 31, 512, 768, 1024, 1 << 40, stream=0)
+    assert e.value.code == "BT_ERR_ARG"
+    bt.bt_free(h)

@@ -1,0 +1,70 @@
+"""Host-side logic of bench.py (no GPU): the algorithmic byte count against
+the oracle, the IQM statistic (Eq. 2), and the max-over-ranks reduction of
+the replicas-only multi-GPU timing on two gloo ranks."""
+from __future__ import annotations
+
+import os
+import socket
+
+import numpy as np
+import pytest
+
+import bench
+from oracle import OracleTree
+from paper_2604_21117_gb300 import workloads as W
+
+
+@pytest.mark.parametrize("m,n,nq,zipf", [(16, 20_000, 3000, None), (32, 100_000, 20_000, 1.1),
+                                         (8, 5_000, 777, None), (64, 300_000, 50_000, None)])
+def test_touched_counts_match_oracle(m, n, nq, zipf):
+    keys = W.uniform_keys(n, 64, seed=n)
+    vals = W.rank_values(n, 64)
+    o = OracleTree(keys, vals, m)
+    q = W.make_queries(keys, nq, 0.9, seed=nq, width_bits=64, zipf_s=zipf)
+    counts, sectors = bench.touched(keys, o.level_nodes(), m, q)
+    oc, osec = o.touched(q)
+    assert counts == oc and sectors == osec
+
+
+def test_iqm_eq2_hand_values():
+    # n = 8: drop the lowest and highest two, mean of the middle four
+    assert bench.iqm([8, 1, 7, 2, 6, 3, 5, 4]) == 4.5
+    assert bench.iqm([10, 10, 10, 10]) == 10.0
+    # n = 12: middle six of 1..12 are 4..9
+    assert bench.iqm(list(range(1, 13))) == 6.5
+    # outliers in the outer quartiles do not move it
+    assert bench.iqm([1, 2, 3, 4, 5, 6, 7, 1000]) == 4.5
+
+
+def test_algorithmic_bytes_formula():
+    # two levels, 3 + 10 distinct nodes of 32 slots x 8 B, 7 value sectors,
+    # batch of 100 (8 B query + 4 B index in, 8 B value + 1 B flag out)
+    assert bench.descend_algorithmic_bytes([3, 10], 7, 32, 8, 8, 100) == 13 * 256 + 7 * 32 + 100 * 21
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _rank_main(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    import torch.distributed as dist
+    bench.dist_init(world, "gloo")
+    t = bench.reduce_max(1.5 + rank, world)
+    bench.barrier(world)
+    out[rank] = t
+    dist.destroy_process_group()
+
+
+def test_reduce_max_over_two_gloo_ranks():
+    import torch.multiprocessing as mp
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    port = _free_port()
+    mp.start_processes(_rank_main, args=(2, port, out), nprocs=2, start_method="spawn")
+    assert dict(out) == {0: 2.5, 1: 2.5}
