@@ -368,9 +368,9 @@ def run_ours(a):
         traffic = NCU_DESCEND_TRAFFIC["bytes_per_launch"]
     step_gbs = statistics.fmean(node_bytes) / (statistics.fmean(step_ms) / 1e3) / 1e9
     passes = bt.bt_sort_passes(tree.handle, B, sort_bits)
-    # our kernels per step: radix histogram + scan + one scatter per pass (or
-    # one copy kernel when the sort is skipped), then the descent
-    launches_per_step = (2 + passes if passes else 1) + 1
+    # our kernels per step: the sort's histogram kernel and one scatter kernel
+    # per pass (or one copy kernel when the sort is skipped), then the descent
+    launches_per_step = (1 + passes if passes else 1) + 1
     sdev = sorted(step_ms)
 
     line = {

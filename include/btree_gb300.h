@@ -190,6 +190,14 @@ bt_status bt_sort_batch(const bt_tree *tree, const void *d_queries, uint64_t nq,
                         void *d_sorted_queries, uint32_t *d_sorted_index, void *d_workspace,
                         uint64_t ws_bytes, bt_stream stream);
 
+/* Status of the last sort that ran in this workspace (bt_search_batch,
+ * bt_search_batch_ex or bt_sort_batch with the same tree and nq): BT_OK, or
+ * BT_ERR_TIMEOUT if a bounded wait of the sort's look-back gave up (the
+ * results of that search are then invalid).  Synchronous: reads one word of
+ * the workspace after the device has finished all work.  A search that did
+ * not sort leaves the word as the previous sort left it. */
+bt_status bt_workspace_status(const bt_tree *tree, const void *d_workspace, uint64_t nq);
+
 /* Number of 8-bit radix passes bt_sort_batch / bt_search_batch would run
  * for this tree, batch size and sort_bits (0 = no sort).  -1 on a NULL tree. */
 int32_t bt_sort_passes(const bt_tree *tree, uint64_t nq, int32_t sort_bits);

@@ -31,7 +31,7 @@ STATUS = {0: "BT_OK", 1: "BT_ERR_ARG", 2: "BT_ERR_UNSORTED", 3: "BT_ERR_DUPLICAT
 
 # Every symbol include/btree_gb300.h declares.
 EXPORTED = ("bt_build", "bt_free", "bt_tree_info", "bt_tree_copy_image", "bt_search_workspace_bytes",
-            "bt_search_batch", "bt_search_batch_ex", "bt_sort_batch", "bt_descend_sorted", "bt_sort_passes",
+            "bt_search_batch", "bt_search_batch_ex", "bt_sort_batch", "bt_descend_sorted", "bt_sort_passes", "bt_workspace_status",
             "bt_search_host_workspace_bytes",
             "bt_search_batch_host", "bt_status_str", "bt_last_error_detail")
 
@@ -71,6 +71,8 @@ _lib.bt_sort_batch.restype = _i
 _lib.bt_sort_batch.argtypes = [_vp, _vp, _u64, ctypes.c_int32, _vp, _vp, _vp, _u64, _vp]
 _lib.bt_sort_passes.restype = ctypes.c_int32
 _lib.bt_sort_passes.argtypes = [_vp, _u64, ctypes.c_int32]
+_lib.bt_workspace_status.restype = _i
+_lib.bt_workspace_status.argtypes = [_vp, _vp, _u64]
 _lib.bt_descend_sorted.restype = _i
 _lib.bt_descend_sorted.argtypes = [_vp, _vp, _vp, _u64, _vp, _vp, _vp, _vp]
 _lib.bt_search_batch_host.restype = _i
@@ -192,6 +194,14 @@ def bt_sort_batch(tree: int, d_queries, nq: int, sort_bits: int, d_sorted_querie
 
 def bt_sort_passes(tree: int, nq: int, sort_bits: int = -1) -> int:
     return int(_lib.bt_sort_passes(tree, nq, sort_bits))
+
+
+def bt_workspace_status(tree: int, d_workspace, nq: int) -> int:
+    """0 (BT_OK) or 7 (BT_ERR_TIMEOUT) for the last sort in this workspace."""
+    st = int(_lib.bt_workspace_status(tree, _dptr(d_workspace), nq))
+    if st not in (0, 7):
+        _check("bt_workspace_status", st)
+    return st
 
 
 def bt_descend_sorted(tree: int, d_queries, d_index, nq: int, d_out_vals, d_out_found,

@@ -28,6 +28,8 @@ struct DevTree {
     int height;
     int m;
     int key_bytes, val_bytes;
+    int pin_levels;      // top levels copied to shared memory by the descent
+    uint32_t pin_bytes;  // bytes from the root's block to the end of those levels
 };
 
 }  // namespace btgb

@@ -123,6 +123,15 @@ extern "C" bt_status bt_build(const void *h_keys, const void *h_vals, uint64_t n
     if (h > 0) off = align_up(off + up[0] * m * vb, 256);
     t->info.device_bytes = off;
 
+    // Top levels small enough for the descent to keep in shared memory
+    // (whole levels, root first, never the leaves; 16 KB at most).
+    for (int l = 0; l + 1 < h; ++l) {
+        const uint64_t end = t->info.level_key_offset[l] + d.nodes[l] * m * kb;
+        if (end > 16384) break;
+        d.pin_levels = l + 1;
+        d.pin_bytes = static_cast<uint32_t>((end + 15) / 16 * 16);
+    }
+
     // Shape arithmetic: children (or keys, for leaves) per node.
     for (int l = 0; l < h; ++l) {
         const uint64_t N = d.nodes[l];

@@ -24,6 +24,7 @@
 #include <cstdint>
 
 #include "bt_internal.h"
+#include "radix_sort.cuh"
 
 namespace btgb {
 
@@ -53,177 +54,76 @@ __device__ __forceinline__ unsigned lanemask_lt()
     return r;
 }
 
-// Normalised sort field of a query: its offset above the smallest key,
-// clamped to the key range, shifted right so `bits` leading bits remain.
-// Monotone in the query, so sorting by it is a partial sort by key.
-struct SortNorm {
-    uint64_t kmin;
-    uint64_t range;
-    int shift;
-    int passes;
-};
-
-template <typename K>
-__device__ __forceinline__ uint32_t sort_digit(K q, const SortNorm &s, int pass)
-{
-    const uint64_t x = static_cast<uint64_t>(q);
-    uint64_t nk = (x <= s.kmin) ? 0 : x - s.kmin;
-    if (nk > s.range) nk = s.range;
-    return static_cast<uint32_t>((nk >> (s.shift + 8 * pass)) & 0xFFu);
-}
-
-// ------------------------------------------------------- radix sort (a2)
-//
-// Classic stable LSD radix sort with 8-bit digits in three kernels: per-tile
-// histograms of every pass's digit (one read of the queries), a scan of each
-// pass's (digit, tile) count matrix in digit-major order, and one stable
-// scatter per pass.
-
-constexpr int kSortTile = 4096;
-constexpr int kSortThreads = 512;
-constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kSortPerWarp = kSortTile / kSortWarps;  // 256 = 8 rounds of 32
-constexpr int kMaxPasses = 8;
-
-template <typename K>
-__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const K *__restrict__ q, uint64_t nq,
-                                                             SortNorm sn, uint32_t *__restrict__ counts,
-                                                             uint32_t ntiles)
-{
-    __shared__ uint32_t h[kMaxPasses * 256];
-    for (int i = threadIdx.x; i < sn.passes * 256; i += blockDim.x) h[i] = 0;
-    __syncthreads();
-    const uint64_t base = static_cast<uint64_t>(blockIdx.x) * kSortTile;
-    for (int e = threadIdx.x; e < kSortTile; e += blockDim.x) {
-        const uint64_t pos = base + e;
-        const bool valid = pos < nq;
-        const unsigned vm = __ballot_sync(0xffffffffu, valid);
-        if (valid) {
-            const K key = q[pos];
-            for (int p = 0; p < sn.passes; ++p) {
-                const uint32_t d = sort_digit(key, sn, p);
-                const unsigned same = __match_any_sync(vm, d);
-                if ((same & lanemask_lt()) == 0) atomicAdd(&h[p * 256 + d], __popc(same));
-            }
-        }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < sn.passes * 256; i += blockDim.x)
-        counts[static_cast<uint64_t>(i) * ntiles + blockIdx.x] = h[i];
-}
-
-// Exclusive scan of one pass's [256][ntiles] count matrix (one CTA per pass).
-__global__ void __launch_bounds__(1024) k_radix_scan(uint32_t *__restrict__ counts, uint32_t ntiles)
-{
-    __shared__ uint32_t warp_tot[32];
-    uint32_t *c = counts + static_cast<uint64_t>(blockIdx.x) * 256u * ntiles;
-    const uint64_t total = 256ull * ntiles;
-    const uint64_t per = (total + blockDim.x - 1) / blockDim.x;
-    const uint64_t lo = threadIdx.x * per;
-    const uint64_t hi = lo + per < total ? lo + per : total;
-    uint32_t sum = 0;
-    for (uint64_t i = lo; i < hi; ++i) sum += c[i];
-    // block-wide exclusive scan of the per-thread sums
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t x = sum;
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) warp_tot[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t w = (lane < (blockDim.x >> 5)) ? warp_tot[lane] : 0;
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += y;
-        }
-        warp_tot[lane] = w;  // inclusive
-    }
-    __syncthreads();
-    uint32_t run = x - sum + (warp > 0 ? warp_tot[warp - 1] : 0);
-    for (uint64_t i = lo; i < hi; ++i) {
-        const uint32_t v = c[i];
-        c[i] = run;
-        run += v;
-    }
-}
-
-// Stable scatter of one pass.  Warp w of tile t owns tile elements
-// [w*256, (w+1)*256) and ranks them in order, 32 at a time, against
-// warp-private digit counters; a per-digit scan over the warps and the
-// tile's global digit offsets then give every element its output slot.
-template <typename K>
-__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
-    const K *__restrict__ qin, const uint32_t *__restrict__ iin, K *__restrict__ qout,
-    uint32_t *__restrict__ iout, uint64_t nq, SortNorm sn, int pass,
-    const uint32_t *__restrict__ offs, uint32_t ntiles)
-{
-    __shared__ uint32_t wh[kSortWarps][256];
-    __shared__ uint32_t toff[256];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < kSortWarps * 256; i += blockDim.x) (&wh[0][0])[i] = 0;
-    for (int i = threadIdx.x; i < 256; i += blockDim.x)
-        toff[i] = offs[static_cast<uint64_t>(i) * ntiles + blockIdx.x];
-    __syncthreads();
-
-    constexpr int R = kSortPerWarp / 32;
-    K key[R];
-    uint32_t idx[R], dig[R], rank[R];
-    const uint64_t base = static_cast<uint64_t>(blockIdx.x) * kSortTile + warp * kSortPerWarp;
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const uint64_t pos = base + r * 32 + lane;
-        const bool valid = pos < nq;
-        if (valid) {
-            key[r] = qin[pos];
-            idx[r] = iin ? iin[pos] : static_cast<uint32_t>(pos);
-        }
-    }
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const uint64_t pos = base + r * 32 + lane;
-        const bool valid = pos < nq;
-        const unsigned vm = __ballot_sync(0xffffffffu, valid);
-        unsigned same = 0;
-        if (valid) {
-            dig[r] = sort_digit(key[r], sn, pass);
-            same = __match_any_sync(vm, dig[r]);
-            rank[r] = wh[warp][dig[r]] + __popc(same & lanemask_lt());
-        }
-        __syncwarp();
-        if (valid && (same & lanemask_lt()) == 0) wh[warp][dig[r]] += __popc(same);
-        __syncwarp();
-    }
-    __syncthreads();
-    for (int d = threadIdx.x; d < 256; d += blockDim.x) {
-        uint32_t run = 0;
-        for (int w = 0; w < kSortWarps; ++w) {
-            const uint32_t v = wh[w][d];
-            wh[w][d] = run;
-            run += v;
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const uint64_t pos = base + r * 32 + lane;
-        if (pos < nq) {
-            const uint32_t o = toff[dig[r]] + wh[warp][dig[r]] + rank[r];
-            qout[o] = key[r];
-            iout[o] = idx[r];
-        }
-    }
-}
-
 // -------------------------------------------- level-wise descent (a3-a5)
+//
+// Persistent blocks of kDescWarps warps.  Each block first copies the top
+// levels of the tree (as many whole levels as fit kPinBudget bytes, never
+// the leaves) into shared memory once; a warp then loops over chunks of 32
+// consecutive queries of the (sorted) batch, prefetching the next chunk's
+// queries and output positions while it works on the current one.  Per
+// level below the pinned ones, the warp's distinct nodes are staged into
+// its shared-memory slots (rounds of `stage_slots` nodes) before the binary
+// searches.
 
-constexpr int kDescWarps = 4;
+constexpr int kDescWarps = 8;
+constexpr int kPinBudget = 16384;
 
 template <typename K, int M>
-constexpr int desc_smem_bytes()
+constexpr int stage_slots()
 {
-    return kDescWarps * (32 * M * static_cast<int>(sizeof(K)) + 32 * 4);
+    return (M * static_cast<int>(sizeof(K)) >= 512) ? 8 : 16;
+}
+
+template <typename K, int M>
+constexpr int desc_smem_fixed()
+{
+    return kDescWarps * (stage_slots<K, M>() * M * static_cast<int>(sizeof(K)) + 32 * 4);
+}
+
+// Number of slots of a node block holding a key smaller than `key`: the
+// child rank at an inner node (the first separator the key is <= to), the
+// only possible match position at a leaf.  Slot M-1 is always padding
+// (all-ones), so log2(M) probes of a branchless binary search suffice.
+template <typename K, int M>
+__device__ __forceinline__ int block_rank(const K *blk, K key)
+{
+    int r = 0;
+#pragma unroll
+    for (int hlf = M / 2; hlf >= 1; hlf >>= 1)
+        if (blk[r + hlf - 1] < key) r += hlf;
+    return r;
+}
+
+// The distinct node ids among the warp's 32 lanes -- the paper's FIFO
+// entries (node address, number of queries) for this warp.  Writes them to
+// list[0..U) and gives each lane the position `slot` of its own node there.
+// A sorted batch keeps a warp's nodes within a narrow range, handled with
+// warp reductions and a 32-bit presence mask; a wider range falls back to
+// warp match.  Every lane of the warp must call it.
+__device__ __forceinline__ void warp_distinct(uint32_t node, int lane, uint32_t *list, int &U, int &slot)
+{
+    const uint32_t nmin = __reduce_min_sync(0xffffffffu, node);
+    const uint32_t nmax = __reduce_max_sync(0xffffffffu, node);
+    if (nmax - nmin < 32u) {
+        const unsigned bit = 1u << (node - nmin);
+        const unsigned mask = __reduce_or_sync(0xffffffffu, bit);
+        U = __popc(mask);
+        slot = __popc(mask & (bit - 1u));
+        if ((mask >> lane) & 1u) list[__popc(mask & ((1u << lane) - 1u))] = nmin + lane;
+    } else {
+        const unsigned same = __match_any_sync(0xffffffffu, node);
+        const int leader = __ffs(same) - 1;
+        const unsigned leaders = __ballot_sync(0xffffffffu, lane == leader);
+        U = __popc(leaders);
+        slot = __popc(leaders & ((1u << leader) - 1u));
+        if (lane == leader) list[slot] = node;
+    }
+}
+
+__device__ __forceinline__ uint32_t child_of(const DevTree &t, int l, uint32_t node, int r)
+{
+    const uint64_t base = t.cbase[l], rem = t.crem[l];
+    return static_cast<uint32_t>(node * base + (node < rem ? node : rem) + r);
 }
 
 template <typename K, typename V, int M, bool COUNT>
@@ -233,59 +133,97 @@ __global__ void __launch_bounds__(kDescWarps * 32) k_descend(
 {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int CH = M * static_cast<int>(sizeof(K)) / 16;  // 16-byte chunks per node block
+    constexpr int SLOTS = stage_slots<K, M>();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    K *stage = reinterpret_cast<K *>(smem) + warp * 32 * M;
-    uint32_t *list = reinterpret_cast<uint32_t *>(smem + kDescWarps * 32 * M * sizeof(K)) + warp * 32;
-    const uint64_t nchunks = (nq + 31) / 32;
-    const int H = t.height;
+    const uint32_t pin_bytes = t.pin_bytes;
+    unsigned char *pin = smem;
+    K *stage = reinterpret_cast<K *>(smem + pin_bytes) + warp * SLOTS * M;
+    uint32_t *list = reinterpret_cast<uint32_t *>(smem + pin_bytes + kDescWarps * SLOTS * M * sizeof(K)) + warp * 32;
 
-    for (uint64_t c = static_cast<uint64_t>(blockIdx.x) * kDescWarps + warp; c < nchunks;
-         c += static_cast<uint64_t>(gridDim.x) * kDescWarps) {
+    // Top levels, pinned once per block.
+    const unsigned char *top = static_cast<const unsigned char *>(t.keys[0]);
+    for (uint32_t i = threadIdx.x * 16u; i < pin_bytes; i += blockDim.x * 16u) cp_async16_ca(pin + i, top + i);
+    cp_async_wait_all();
+    __syncthreads();
+
+    const uint64_t nchunks = (nq + 31) / 32;
+    const uint64_t stride = static_cast<uint64_t>(gridDim.x) * kDescWarps;
+    const int H = t.height, P = t.pin_levels;
+    uint64_t c = static_cast<uint64_t>(blockIdx.x) * kDescWarps + warp;
+    if (c >= nchunks) return;
+
+    // Tail lanes follow lane 0's query so they never add a node fetch.
+    K key_n;
+    uint32_t dst_n;
+    {
+        const uint64_t pos = c * 32 + lane;
+        const bool v = pos < nq;
+        key_n = q[v ? pos : c * 32];
+        dst_n = v ? (qidx ? qidx[pos] : static_cast<uint32_t>(pos)) : 0u;
+    }
+    for (;;) {
         const uint64_t pos = c * 32 + lane;
         const bool valid = pos < nq;
-        // Tail lanes follow lane 0's query so they never add a node fetch.
-        const K key = q[valid ? pos : c * 32];
-        const uint32_t dst = valid ? (qidx ? qidx[pos] : static_cast<uint32_t>(pos)) : 0u;
-        uint32_t node = 0;
+        const K key = key_n;
+        const uint32_t dst = dst_n;
+        const uint64_t cn = c + stride;
+        if (cn < nchunks) {  // prefetch the next chunk
+            const uint64_t pn = cn * 32 + lane;
+            const bool vn = pn < nq;
+            key_n = q[vn ? pn : cn * 32];
+            dst_n = vn ? (qidx ? qidx[pn] : static_cast<uint32_t>(pn)) : 0u;
+        }
 
-        for (int l = 0; l < H; ++l) {
+        uint32_t node = 0;
+        int l = 0;
+        for (; l < P; ++l) {  // pinned levels: search the block's shared copy
+            if (COUNT) {
+                int U, slot;
+                warp_distinct(node, lane, list, U, slot);
+                __syncwarp();
+                if (lane == 0) atomicAdd(fetch + l, static_cast<unsigned long long>(U));
+            }
+            const K *blk = reinterpret_cast<const K *>(
+                               pin + (static_cast<const unsigned char *>(t.keys[l]) - top)) +
+                           static_cast<uint64_t>(node) * M;
+            node = child_of(t, l, node, block_rank<K, M>(blk, key));
+        }
+        for (; l < H; ++l) {
             const K *lk = static_cast<const K *>(t.keys[l]);
-            // Distinct nodes among the warp's queries: one leader per node.
-            const unsigned same = __match_any_sync(0xffffffffu, node);
-            const int leader = __ffs(same) - 1;
-            const unsigned leaders = __ballot_sync(0xffffffffu, lane == leader);
-            const int U = __popc(leaders);
-            const int slot = __popc(leaders & ((1u << leader) - 1u));
-            if (lane == leader) list[slot] = node;
+            const bool last = (l + 1 == H);
+            int U, slot;
+            warp_distinct(node, lane, list, U, slot);
             if (COUNT && lane == 0) atomicAdd(fetch + l, static_cast<unsigned long long>(U));
             __syncwarp();
-            // Stage each distinct node's key block once.
-            const bool last = (l + 1 == H);
-            for (int i = lane; i < U * CH; i += 32) {
-                const int u = i / CH, part = i - u * CH;
-                const unsigned char *src = reinterpret_cast<const unsigned char *>(
-                                               lk + static_cast<uint64_t>(list[u]) * M) + part * 16;
-                unsigned char *dstp = reinterpret_cast<unsigned char *>(stage + u * M) + part * 16;
-                if (last)
-                    cp_async16_cg(dstp, src);
-                else
-                    cp_async16_ca(dstp, src);
-            }
-            cp_async_wait_all();
-            __syncwarp();
-            // Child rank = number of slots holding a key < query.  Slot M-1
-            // is always padding (all-ones), so log2(M) probes suffice.
-            const K *blk = stage + slot * M;
             int r = 0;
-#pragma unroll
-            for (int hlf = M / 2; hlf >= 1; hlf >>= 1)
-                if (blk[r + hlf - 1] < key) r += hlf;
+            bool eq = false;
+            for (int rb = 0; rb < U; rb += SLOTS) {
+                const int nu = (U - rb < SLOTS) ? U - rb : SLOTS;
+                // Stage each distinct node's key block once.
+                for (int i = lane; i < nu * CH; i += 32) {
+                    const int u = i / CH, part = i - u * CH;
+                    const unsigned char *src = reinterpret_cast<const unsigned char *>(
+                                                   lk + static_cast<uint64_t>(list[rb + u]) * M) + part * 16;
+                    unsigned char *dp = reinterpret_cast<unsigned char *>(stage + u * M) + part * 16;
+                    if (last)
+                        cp_async16_cg(dp, src);
+                    else
+                        cp_async16_ca(dp, src);
+                }
+                cp_async_wait_all();
+                __syncwarp();
+                if (slot >= rb && slot < rb + nu) {
+                    const K *blk = stage + (slot - rb) * M;
+                    r = block_rank<K, M>(blk, key);
+                    eq = (blk[r] == key);
+                }
+                __syncwarp();
+            }
             if (!last) {
-                const uint64_t base = t.cbase[l], rem = t.crem[l];
-                node = static_cast<uint32_t>(node * base + (node < rem ? node : rem) + r);
+                node = child_of(t, l, node, r);
             } else {
                 const uint64_t cnt = t.cbase[l] + (node < t.crem[l] ? 1u : 0u);
-                const bool hit = (static_cast<uint64_t>(r) < cnt) && (blk[r] == key);
+                const bool hit = (static_cast<uint64_t>(r) < cnt) && eq;
                 V val = static_cast<V>(~static_cast<V>(0));
                 if (hit) val = static_cast<const V *>(t.vals)[static_cast<uint64_t>(node) * M + r];
                 if (valid) {
@@ -293,8 +231,9 @@ __global__ void __launch_bounds__(kDescWarps * 32) k_descend(
                     out_f[dst] = hit ? 1 : 0;
                 }
             }
-            __syncwarp();
         }
+        if (cn >= nchunks) break;
+        c = cn;
     }
 }
 
@@ -315,9 +254,12 @@ static inline uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
 static inline uint32_t sort_tiles(uint64_t nq) { return static_cast<uint32_t>((nq + kSortTile - 1) / kSortTile); }
 
 struct WsLayout {
-    uint64_t qa, ia, qb, ib, counts, total;
+    uint64_t qa, ia, qb, ib, meta, status, total;
 };
 
+// Workspace: two ping-pong (query, position) buffers, then the sort's
+// metadata block (global digit histograms, tile counters, error word) and
+// the per-tile look-back status words.
 static WsLayout ws_layout(int kb, uint64_t nq)
 {
     WsLayout w;
@@ -330,10 +272,22 @@ static WsLayout ws_layout(int kb, uint64_t nq)
     o = align256(o + nq * kb);
     w.ib = o;
     o = align256(o + nq * 4);
-    w.counts = o;
-    o = align256(o + static_cast<uint64_t>(kMaxPasses) * 256u * sort_tiles(nq) * 4u);
+    w.meta = o;
+    o = align256(o + (kMaxPasses * 256 + kMaxPasses + 1) * 4);
+    w.status = o;
+    o = align256(o + static_cast<uint64_t>(kMaxPasses) * sort_tiles(nq) * 256u * 8u);
     w.total = nq ? o : 0;
     return w;
+}
+
+static SortMeta sort_meta(unsigned char *ws, const WsLayout &w)
+{
+    SortMeta m;
+    m.ghist = reinterpret_cast<uint32_t *>(ws + w.meta);
+    m.tile_ctr = m.ghist + kMaxPasses * 256;
+    m.err = m.tile_ctr + kMaxPasses;
+    m.status = reinterpret_cast<unsigned long long *>(ws + w.status);
+    return m;
 }
 
 static int bitlen(uint64_t x) { return x ? 64 - __builtin_clzll(x) : 0; }
@@ -347,15 +301,32 @@ static cudaError_t launch_descend(const DevTree &t, const void *q, const uint32_
                                   void *out_v, uint8_t *out_f, unsigned long long *fetch,
                                   cudaStream_t s)
 {
-    constexpr int smem = desc_smem_bytes<K, M>();
-    static const cudaError_t attr = cudaFuncSetAttribute(
-        k_descend<K, V, M, COUNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    constexpr int fixed = desc_smem_fixed<K, M>();
+    constexpr int threads = kDescWarps * 32;
+    auto kern = k_descend<K, V, M, COUNT>;
+    static const cudaError_t attr =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, fixed + kPinBudget);
     if (attr != cudaSuccess) return attr;
+    const int smem = fixed + static_cast<int>(t.pin_bytes);
+    // resident blocks per SM for this shared-memory size (cached per size)
+    static int occ_cache[kPinBudget / 256 + 2] = {0};
+    const int key = static_cast<int>((t.pin_bytes + 255) / 256);
+    if (occ_cache[key] == 0) {
+        int b = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, threads, fixed + key * 256);
+        if (e != cudaSuccess) return e;
+        occ_cache[key] = b > 0 ? b : 1;
+    }
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
     const uint64_t chunks = (nq + 31) / 32;
     uint64_t grid = (chunks + kDescWarps - 1) / kDescWarps;
-    if (grid > (1u << 30)) grid = 1u << 30;
-    k_descend<K, V, M, COUNT><<<static_cast<unsigned>(grid), kDescWarps * 32, smem, s>>>(
-        t, static_cast<const K *>(q), qidx, nq, static_cast<V *>(out_v), out_f, fetch);
+    const uint64_t cap = static_cast<uint64_t>(sms) * occ_cache[key];
+    if (grid > cap) grid = cap;
+    kern<<<static_cast<unsigned>(grid), threads, smem, s>>>(t, static_cast<const K *>(q), qidx, nq,
+                                                           static_cast<V *>(out_v), out_f, fetch);
     return cudaGetLastError();
 }
 
@@ -409,9 +380,16 @@ static cudaError_t radix_sort(const K *q, uint64_t nq, const SortNorm &sn, unsig
                               const WsLayout &w, K *dst_q, uint32_t *dst_i, cudaStream_t s)
 {
     const uint32_t ntiles = sort_tiles(nq);
-    uint32_t *counts = reinterpret_cast<uint32_t *>(ws + w.counts);
-    k_radix_hist<K><<<ntiles, kSortThreads, 0, s>>>(q, nq, sn, counts, ntiles);
-    k_radix_scan<<<sn.passes, 1024, 0, s>>>(counts, ntiles);
+    const SortMeta meta = sort_meta(ws, w);
+    // histograms, tile counters, error word and the used status words start at zero
+    cudaError_t e = cudaMemsetAsync(ws + w.meta, 0,
+                                    (w.status - w.meta) + static_cast<uint64_t>(sn.passes) * ntiles * 256u * 8u, s);
+    if (e != cudaSuccess) return e;
+    constexpr int smem = sort_pass_smem_bytes<K>();
+    static const cudaError_t attr =
+        cudaFuncSetAttribute(k_sort_pass<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (attr != cudaSuccess) return attr;
+    k_sort_hist<K><<<ntiles, kSortThreads, 0, s>>>(q, nq, sn, meta.ghist);
     K *qa = reinterpret_cast<K *>(ws + w.qa), *qb = reinterpret_cast<K *>(ws + w.qb);
     uint32_t *ia = reinterpret_cast<uint32_t *>(ws + w.ia), *ib = reinterpret_cast<uint32_t *>(ws + w.ib);
     const K *src_q = q;
@@ -420,8 +398,7 @@ static cudaError_t radix_sort(const K *q, uint64_t nq, const SortNorm &sn, unsig
         const bool final_pass = (p + 1 == sn.passes);
         K *dq = final_pass ? dst_q : ((p & 1) ? qb : qa);
         uint32_t *di = final_pass ? dst_i : ((p & 1) ? ib : ia);
-        k_radix_scatter<K><<<ntiles, kSortThreads, 0, s>>>(
-            src_q, src_i, dq, di, nq, sn, p, counts + static_cast<uint64_t>(p) * 256u * ntiles, ntiles);
+        k_sort_pass<K><<<ntiles, kSortThreads, smem, s>>>(src_q, src_i, dq, di, nq, sn, p, meta, ntiles);
         src_q = dq;
         src_i = di;
     }
@@ -467,6 +444,22 @@ static SortNorm make_norm(const DevTree &t, int32_t sort_bits, uint64_t nq)
 }  // namespace btgb
 
 using namespace btgb;
+
+extern "C" bt_status bt_workspace_status(const bt_tree *tree, const void *d_workspace, uint64_t nq)
+{
+    if (!tree || !d_workspace) return BT_ERR_ARG;
+    if (nq == 0) return BT_OK;
+    const WsLayout w = ws_layout(tree->dev.key_bytes, nq);
+    uint32_t err = 0;
+    const unsigned char *ws = static_cast<const unsigned char *>(d_workspace);
+    cudaError_t e = cudaMemcpy(&err, ws + w.meta + (kMaxPasses * 256 + kMaxPasses) * 4, 4,
+                               cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        set_error_detail("workspace status read", e);
+        return BT_ERR_CUDA;
+    }
+    return err ? BT_ERR_TIMEOUT : BT_OK;
+}
 
 extern "C" int32_t bt_sort_passes(const bt_tree *tree, uint64_t nq, int32_t sort_bits)
 {

@@ -262,3 +262,17 @@ def test_split_sort_then_descend(bt, kw, sb):
     ov, of, _, _ = o.search(q)
     assert np.array_equal(v.cpu().numpy().astype(np.uint64), ov)
     assert np.array_equal(fo.cpu().numpy(), of)
+
+
+def test_sort_lookback_status_ok_after_searches(bt):
+    """The sort's bounded look-back waits never give up on ordinary input."""
+    keys = W.uniform_keys(100_000, 64, seed=20)
+    vals = W.rank_values(keys.size, 64)
+    tree = bt.BTree(keys, vals, 32)
+    for nq in (4097, 100_000, 1 << 20):
+        q = W.make_queries(keys, nq, 0.9, seed=nq + 1, width_bits=64, zipf_s=1.1)
+        v, f = tree.alloc_outputs(nq)
+        ws, nb = tree.alloc_workspace(nq)
+        for sb in (8, 16, 64):
+            tree.search_into(_to_dev(q), v, f, ws, nb, sort_bits=sb)
+            assert bt.bt_workspace_status(tree.handle, ws, nq) == 0
