@@ -242,6 +242,37 @@ bt_status bt_search_batch_host(const bt_tree *tree, const void *h_queries, uint6
                                void *h_out_vals, uint8_t *h_out_found, void *d_workspace,
                                uint64_t ws_bytes, bt_stream stream);
 
+/*
+ * bt_search_batch_noalloc -- bt_search_batch without a caller workspace and
+ * without any device allocation.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory, such as a
+ * query engine or plugin host that owns every device buffer through its own
+ * arena and hands a library only input and output pointers, or a latency-
+ * critical request path that must not call cudaMalloc/cudaFree (they can
+ * synchronize the whole device).
+ *
+ * Scratch space (sort buffers, histograms, look-back words) is a 2 MiB
+ * file-scope device array inside the library; every GPU that loads the
+ * library holds it until the process exits.  The caller still passes the
+ * queries and the outputs, as for bt_search_batch.
+ *
+ *   nq   at most BT_NOALLOC_MAX_QUERIES; larger batches are rejected with
+ *        BT_ERR_ARG (bt_last_error_detail says why) -- use bt_search_batch
+ *        with a workspace for them.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  The call allocates nothing (no cudaMalloc,
+ * cudaFree or allocating library routine).  All calls share the one array
+ * and it keeps the last call's contents (each search clears what must start
+ * at zero), so calls whose work overlaps on the GPU -- on different streams,
+ * or from different threads -- race and must be serialised by the caller.
+ * Errors: as bt_search_batch, plus BT_ERR_ARG for nq > BT_NOALLOC_MAX_QUERIES.
+ */
+#define BT_NOALLOC_MAX_QUERIES 65536
+bt_status bt_search_batch_noalloc(const bt_tree *tree, const void *d_queries, uint64_t nq,
+                                  void *d_out_vals, uint8_t *d_out_found, bt_stream stream);
+
 /* Static text for a status code. */
 const char *bt_status_str(bt_status status);
 

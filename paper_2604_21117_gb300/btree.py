@@ -33,7 +33,7 @@ STATUS = {0: "BT_OK", 1: "BT_ERR_ARG", 2: "BT_ERR_UNSORTED", 3: "BT_ERR_DUPLICAT
 EXPORTED = ("bt_build", "bt_free", "bt_tree_info", "bt_tree_copy_image", "bt_search_workspace_bytes",
             "bt_search_batch", "bt_search_batch_ex", "bt_sort_batch", "bt_descend_sorted", "bt_sort_passes", "bt_workspace_status",
             "bt_search_host_workspace_bytes",
-            "bt_search_batch_host", "bt_status_str", "bt_last_error_detail")
+            "bt_search_batch_host", "bt_search_batch_noalloc", "bt_status_str", "bt_last_error_detail")
 
 
 class bt_info(ctypes.Structure):
@@ -77,6 +77,8 @@ _lib.bt_descend_sorted.restype = _i
 _lib.bt_descend_sorted.argtypes = [_vp, _vp, _vp, _u64, _vp, _vp, _vp, _vp]
 _lib.bt_search_batch_host.restype = _i
 _lib.bt_search_batch_host.argtypes = [_vp, _vp, _u64, _vp, _vp, _vp, _u64, _vp]
+_lib.bt_search_batch_noalloc.restype = _i
+_lib.bt_search_batch_noalloc.argtypes = [_vp, _vp, _u64, _vp, _vp, _vp]
 _lib.bt_status_str.restype = ctypes.c_char_p
 _lib.bt_status_str.argtypes = [_i]
 _lib.bt_last_error_detail.restype = ctypes.c_char_p
@@ -225,6 +227,19 @@ def bt_search_batch_host(tree: int, h_queries, nq: int, h_out_vals, h_out_found,
     st = _lib.bt_search_batch_host(tree, hp(h_queries), nq, hp(h_out_vals), hp(h_out_found),
                                    _dptr(d_workspace), ws_bytes, _stream_handle(stream))
     _check("bt_search_batch_host", st)
+
+
+BT_NOALLOC_MAX_QUERIES = 65536
+
+
+def bt_search_batch_noalloc(tree: int, d_queries, nq: int, d_out_vals, d_out_found, stream=None) -> None:
+    """Search without a workspace or any device allocation, for callers that
+    cannot allocate device memory; the library's own 2 MiB device scratch
+    array is used instead (at most BT_NOALLOC_MAX_QUERIES queries; calls that
+    overlap on the GPU share that array and race)."""
+    st = _lib.bt_search_batch_noalloc(tree, _dptr(d_queries), nq, _dptr(d_out_vals), _dptr(d_out_found),
+                                      _stream_handle(stream))
+    _check("bt_search_batch_noalloc", st)
 
 
 def _torch_dtype(width: int):
