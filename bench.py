@@ -56,6 +56,9 @@ def parse_args(argv=None):
     p.add_argument("--sort-bits", type=int, default=-1)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true", help="skip e2e / small-batch latency legs")
+    p.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain leg")
+    p.add_argument("--no-batching", action="store_true", help="skip the multi-tree batching leg")
+    p.add_argument("--no-serving", action="store_true", help="skip the serving leg")
     return p.parse_args(argv)
 
 
@@ -281,6 +284,251 @@ def cpu_baseline(keys, vals, m, q, budget_s: float = 12.0):
                        f"{build_s:.1f} s untimed")}
 
 
+# ------------------------------------------------------ learned leg
+
+def _time_calls(fn, steps, flush, stream):
+    """Per-call CUDA-event times (us) of fn(), L2 flushed before each call."""
+    import torch
+    out = []
+    for i in range(steps):
+        if flush is not None:
+            flush.fill_(i)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        out.append((e0, e1))
+    torch.cuda.synchronize()
+    return sorted(1e3 * x.elapsed_time(y) for x, y in out)
+
+
+def learned_leg(a, bt, flush, stream):
+    """Plain level-wise search against the learned leaf predictor (PL with
+    256 segments, MLP 1-32-32-1) on 2^24 keys from a mixture of three
+    lognormals, fanout 32, 90% hits, batches of 1024 and 2^20."""
+    import torch
+    n = 1 << 24
+    keys = W.lognormal_mixture_keys(n, seed=W.SEED_BASE + 4)
+    vals = W.rank_values(n, 64)
+    tree = bt.BTree(keys, vals, 32)
+    res = {"workload": f"{n} lognormal-mixture uint64 keys (sigma 1, 2, 0.5), fanout 32, 90% hits"}
+    t0 = time.perf_counter()
+    pl = bt.bt_model_train(tree.handle, bt.BT_MODEL_PL, segments=256)
+    t_pl = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    mlp = bt.bt_model_train(tree.handle, bt.BT_MODEL_MLP, h_init=W.mlp_init_params(W.SEED_BASE + 5),
+                            steps=2000, batch=16384, lr=2e-3, seed=W.SEED_BASE + 6)
+    t_mlp = time.perf_counter() - t0
+    ipl, imlp = bt.bt_model_get_info(pl), bt.bt_model_get_info(mlp)
+    res["models"] = {"pl256": {"max_err_leaves": int(ipl.max_err), "fit_s": t_pl},
+                     "mlp": {"max_err_leaves": int(imlp.max_err), "train_s": t_mlp, "steps": 2000,
+                             "batch": 16384, "final_mse": float(imlp.final_loss)}}
+    for B, steps in ((1024, 300), (1 << 20, 50)):
+        q = torch.from_numpy(W.make_queries(keys, B, 0.9, seed=W.SEED_BASE + 7 + B, width_bits=64)).cuda()
+        nb = tree.workspace_bytes(B)
+        ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        outs = {k: tree.alloc_outputs(B) for k in ("plain", "pl256", "mlp")}
+        calls = {
+            "plain": lambda: bt.bt_search_batch(tree.handle, q, B, *outs["plain"], ws, nb, stream),
+            "pl256": lambda: bt.bt_learned_search_batch(tree.handle, pl, q, B, *outs["pl256"], ws, nb, stream),
+            "mlp": lambda: bt.bt_learned_search_batch(tree.handle, mlp, q, B, *outs["mlp"], ws, nb, stream),
+        }
+        row = {}
+        for name, fn in calls.items():
+            for _ in range(3):
+                fn()
+            us = _time_calls(fn, steps, flush if B > 4096 else None, stream)
+            row[name] = {"lookups_per_s": B / (statistics.fmean(us) / 1e6), "p50_us": us[len(us) // 2],
+                         "p99_us": us[min(len(us) - 1, int(0.99 * len(us)))]}
+        pv, pf = (x.cpu().numpy() for x in outs["plain"])
+        for name in ("pl256", "mlp"):
+            lv, lf = (x.cpu().numpy() for x in outs[name])
+            row[name]["bit_exact_vs_plain"] = bool(np.array_equal(lv, pv) and np.array_equal(lf, pf))
+            row[name]["speedup_vs_plain"] = row[name]["lookups_per_s"] / row["plain"]["lookups_per_s"]
+        # share of warps the model window served (the rest fell back to the descent)
+        sq = torch.empty_like(q)
+        si = torch.empty(B, dtype=torch.int32, device="cuda")
+        bt.bt_sort_batch(tree.handle, q, B, -1, sq, si, ws, nb, stream)
+        for name, mdl in (("pl256", pl), ("mlp", mlp)):
+            st = torch.zeros(2, dtype=torch.int64, device="cuda")
+            v, f = tree.alloc_outputs(B)
+            bt.bt_learned_descend_sorted(tree.handle, mdl, sq, si, B, v, f, st, stream)
+            s0, s1 = (int(x) for x in st.cpu().numpy())
+            row[name]["window_served_frac"] = s0 / max(1, s0 + s1)
+        res[f"batch_{B}"] = row
+    bt.bt_model_free(pl)
+    bt.bt_model_free(mlp)
+    tree.close()
+    return res
+
+
+# ------------------------------------------------------ batching leg
+
+def batching_leg(a, bt, stream, nbatches: int = 10_000):
+    """One graph-captured persistent launch over a work list of many small
+    batches addressed to 4 resident trees (1e3, 1e5, 1e6, 2e7 uint64 keys,
+    fanout and launch settings chosen by the autotuner); batch sizes
+    log-uniform in [1, 1024]; Zipf(0.9) queries with 80% hits."""
+    import torch
+    sizes = [1000, 100_000, 1_000_000, 20_000_000]
+    trees, keysets, tunes = [], [], []
+    t0 = time.perf_counter()
+    for i, n in enumerate(sizes):
+        keys = W.uniform_keys(n, 64, seed=W.SEED_BASE + 20 + i)
+        vals = W.rank_values(n, 64)
+        sample = W.make_queries(keys, 1024, 0.8, seed=W.SEED_BASE + 30 + i, width_bits=64, zipf_s=0.9)
+        h, best = bt.bt_autotune(keys, vals, torch.from_numpy(sample).cuda(), sample.size)
+        trees.append(bt.BTree(None, None, handle=h))
+        keysets.append(keys)
+        tunes.append({"keys": n, "fanout": int(best.fanout), "warps_per_block": int(best.warps_per_block),
+                      "pin_bytes": int(best.pin_bytes), "sample_us": float(best.us_per_batch)})
+    tune_s = time.perf_counter() - t0
+    g = W.rng(W.SEED_BASE + 40)
+    counts = W.log_uniform_batch_sizes(nbatches, seed=W.SEED_BASE + 41)
+    tids = g.integers(0, len(trees), size=nbatches)
+    pools = {}
+    for ti in range(len(trees)):
+        need = int(counts[tids == ti].sum())
+        pools[ti] = W.make_queries(keysets[ti], need, 0.8, seed=W.SEED_BASE + 50 + ti, width_bits=64, zipf_s=0.9)
+    used = {ti: 0 for ti in pools}
+    desc = np.zeros(nbatches, bt.BATCH_DESC_DTYPE)
+    parts, off = [], 0
+    for b in range(nbatches):
+        c, ti = int(counts[b]), int(tids[b])
+        parts.append(pools[ti][used[ti]:used[ti] + c])
+        used[ti] += c
+        desc[b] = (ti, c, off)
+        off += c
+    total = off
+    dq = torch.from_numpy(np.concatenate(parts)).cuda()
+    d_desc = torch.from_numpy(desc.view(np.uint8)).cuda()
+    forest = bt.bt_forest_create(trees)
+    v = torch.empty(total, dtype=torch.uint64, device="cuda")
+    f = torch.empty(total, dtype=torch.uint8, device="cuda")
+    wsb = bt.bt_forest_workspace_bytes(nbatches)
+    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        bt.bt_forest_search(forest, d_desc, nbatches, dq, v, f, ws, wsb, 8, s)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        bt.bt_forest_search(forest, d_desc, nbatches, dq, v, f, ws, wsb, 8, torch.cuda.current_stream())
+    for _ in range(3):
+        graph.replay()
+    torch.cuda.synchronize()
+    reps = 20
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    cur = torch.cuda.current_stream()
+    for e0, e1 in ev:
+        e0.record(cur)
+        graph.replay()
+        e1.record(cur)
+    torch.cuda.synchronize()
+    us = sorted(1e3 * x.elapsed_time(y) for x, y in ev)
+    # correctness of the graph replay against the per-tree single-batch path
+    vv, ff = v.cpu().numpy(), f.cpu().numpy()
+    ok = True
+    for b in range(0, nbatches, 97):
+        c, o, ti = int(desc[b]["count"]), int(desc[b]["offset"]), int(desc[b]["tree"])
+        if c == 0:
+            continue
+        rv, rf = trees[ti].search(dq[o:o + c])
+        ok &= bool(np.array_equal(rv.cpu().numpy(), vv[o:o + c]) and np.array_equal(rf.cpu().numpy(), ff[o:o + c]))
+    # the same work list as one bt_search_batch launch sequence per batch
+    outs = [trees[int(desc[b]["tree"])].alloc_outputs(max(1, int(desc[b]["count"]))) for b in range(nbatches)]
+    wss = {}
+    for ti, t in enumerate(trees):
+        nbt = t.workspace_bytes(1024)
+        wss[ti] = (torch.empty(nbt, dtype=torch.uint8, device="cuda"), nbt)
+
+    def per_batch():
+        for b in range(nbatches):
+            c, o, ti = int(desc[b]["count"]), int(desc[b]["offset"]), int(desc[b]["tree"])
+            if c:
+                bt.bt_search_batch(trees[ti].handle, dq[o:o + c], c, *outs[b], *wss[ti], cur)
+    per_batch()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record(cur)
+    per_batch()
+    e1.record(cur)
+    torch.cuda.synchronize()
+    per_batch_wall = time.perf_counter() - t0
+    per_batch_us = 1e3 * e0.elapsed_time(e1)
+    bt.bt_forest_free(forest)
+    for t in trees:
+        t.close()
+    return {"workload": f"{nbatches} batches, sizes log-uniform 1..1024, over trees of {sizes} uint64 keys, "
+                        "Zipf(0.9) queries, 80% hits",
+            "queries": total, "autotune": tunes, "autotune_s": tune_s,
+            "graph_launch": {"lookups_per_s": total / (statistics.fmean(us) / 1e6), "p50_us": us[len(us) // 2],
+                             "p99_us": us[min(len(us) - 1, int(0.99 * len(us)))], "launches_per_work_list": 2},
+            "per_batch_launches": {"lookups_per_s": total / (per_batch_us / 1e6), "device_us": per_batch_us,
+                                   "host_wall_s": per_batch_wall, "launches": int((counts > 0).sum())},
+            "bit_exact_vs_single_tree_path": ok}
+
+
+# ------------------------------------------------------- serving leg
+
+def serving_leg(a, bt, rates=(1e6, 5e6, 20e6, 50e6), seconds: float = 0.25):
+    """Continuous batching under Poisson arrivals: 2 resident trees (1e6 and
+    2e7 uint64 keys, fanout 32), requests of 1..64 lookups (geometric, mean
+    8), 50 us batching deadline, memory-capped admission; plain search
+    against the learned (PL-256) search."""
+    sizes = [1_000_000, 20_000_000]
+    trees, keysets, models = [], [], []
+    for i, n in enumerate(sizes):
+        keys = W.uniform_keys(n, 64, seed=W.SEED_BASE + 60 + i)
+        trees.append(bt.BTree(keys, W.rank_values(n, 64), 32))
+        keysets.append(keys)
+        models.append(bt.bt_model_train(trees[-1].handle, bt.BT_MODEL_PL, segments=256))
+    out = {"workload": "2 trees (1e6, 2e7 uint64 keys, fanout 32); Poisson arrivals; requests of 1..64 lookups "
+                       "(geometric, mean 8), 80% hits; 50 us deadline; 8 slots; 16 MB in-flight cap",
+           "rates": {}}
+    for rate in rates:
+        nreq = max(1000, int(rate / 8.0 * seconds))
+        seed = W.SEED_BASE + 70 + int(rate // 1e6)
+        cnt = W.geometric_request_sizes(nreq, seed=seed).astype(np.uint32)
+        tid = W.rng(seed).integers(0, 2, size=nreq).astype(np.uint32)
+        pools = [W.make_queries(keysets[i], int(cnt[tid == i].sum()), 0.8, seed=seed + 1 + i, width_bits=64)
+                 for i in range(2)]
+        base = [0, pools[0].size]
+        allk = np.concatenate(pools)
+        koff = np.empty(nreq, np.uint64)
+        cur = [0, 0]
+        for r in range(nreq):
+            i = int(tid[r])
+            koff[r] = base[i] + cur[i]
+            cur[i] += int(cnt[r])
+        t_arr = W.poisson_arrivals(rate / 8.0, nreq, seed=seed + 3)
+        row = {"requests": nreq, "lookups": int(allk.size)}
+        ref = None
+        for mode in ("plain", "learned"):
+            srv = bt.bt_server_create(trees, models if mode == "learned" else None, slots=8, max_batch=8192,
+                                      deadline_us=50.0, mem_cap_bytes=16 << 20)
+            vals = np.zeros(allk.size, np.uint64)
+            found = np.zeros(allk.size, np.uint8)
+            wall = bt.bt_server_run_trace(srv, t_arr, tid, cnt, koff, allk, vals, found)
+            st = bt.bt_server_get_stats(srv)
+            bt.bt_server_destroy(srv)
+            row[mode] = {"lookups_per_s": allk.size / wall, "offered_lookups_per_s": rate,
+                         "p50_us": float(st.p50_us), "p99_us": float(st.p99_us), "batches": int(st.batches),
+                         "mean_batch": allk.size / max(1, st.batches), "max_inflight": int(st.max_inflight)}
+            if ref is None:
+                ref = (vals, found)
+            else:
+                row[mode]["bit_exact_vs_plain"] = bool(np.array_equal(vals, ref[0]) and np.array_equal(found, ref[1]))
+        out["rates"][f"{rate / 1e6:g}M"] = row
+    for m in models:
+        bt.bt_model_free(m)
+    for t in trees:
+        t.close()
+    return out
+
+
 # ---------------------------------------------------------- our arm
 
 def run_ours(a):
@@ -367,10 +615,10 @@ def run_ours(a):
     if NCU_DESCEND_TRAFFIC["search_cu_sha256"] == src_sha256():
         traffic = NCU_DESCEND_TRAFFIC["bytes_per_launch"]
     step_gbs = statistics.fmean(node_bytes) / (statistics.fmean(step_ms) / 1e3) / 1e9
-    passes = bt.bt_sort_passes(tree.handle, B, sort_bits)
-    # our kernels per step: the sort's histogram kernel and one scatter kernel
-    # per pass (or one copy kernel when the sort is skipped), then the descent
-    launches_per_step = (1 + passes if passes else 1) + 1
+    sort_k = bt.bt_sort_launches(tree.handle, B, sort_bits)
+    # our kernels per step: the sort's kernels (or one copy kernel when the
+    # sort is skipped), then the descent
+    launches_per_step = (sort_k if sort_k else 1) + 1
     sdev = sorted(step_ms)
 
     line = {
@@ -445,6 +693,13 @@ def run_ours(a):
             lat[f"b{b}"] = {"p50_us": us[len(us) // 2], "p99_us": us[int(0.99 * len(us))],
                             "lookups_per_s": b / (statistics.fmean(us) / 1e6)}
         line["small_batch_latency"] = lat
+
+    if not a.no_extras and not a.no_learned:
+        line["learned"] = learned_leg(a, bt, flush, stream)
+    if not a.no_extras and not a.no_batching:
+        line["batching"] = batching_leg(a, bt, stream)
+    if not a.no_extras and not a.no_serving:
+        line["serving"] = serving_leg(a, bt)
 
     sampler.stop()
     line["clocks"] = sampler.summary()

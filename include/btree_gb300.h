@@ -61,6 +61,9 @@ typedef enum bt_status {
 /* Opaque, immutable after bt_build. */
 typedef struct bt_tree bt_tree;
 
+/* Opaque learned leaf predictor of one tree (see bt_model_train). */
+typedef struct bt_model bt_model;
+
 /* Shape of a built tree.  Level 0 is the root, level height-1 the leaves. */
 typedef struct bt_info {
     uint32_t height;                       /* number of levels; 0 for an empty tree */
@@ -128,9 +131,9 @@ uint64_t bt_search_workspace_bytes(const bt_tree *tree, uint64_t nq);
 typedef struct bt_search_opts {
     /* How many leading bits of the normalised query key the batch is
      * radix-sorted on before the descent (Sec. IV-A sorts the batch so that
-     * queries for one node are adjacent): -1 lets the library choose from nq
-     * and the tree, 0 skips the sort, 1..64 forces that many bits (rounded up
-     * to whole 8-bit radix passes, capped at the key width). */
+     * queries for one node are adjacent; see bt_sort_batch for the order
+     * obtained): -1 lets the library choose from nq and the tree, 0 skips
+     * the sort, 1..64 forces that many bits (capped at the key range). */
     int32_t sort_bits;
     /* If non-NULL: device array of `height` counters to which the search
      * adds, per level, how many node key blocks it fetched -- the quantity
@@ -169,15 +172,20 @@ bt_status bt_search_batch_ex(const bt_tree *tree, const void *d_queries, uint64_
                              bt_stream stream);
 
 /*
- * bt_sort_batch -- the first step of a search on its own: the on-device LSD
- * radix sort of the batch (Sec. IV-A: queries are sorted so that those
- * routed to one node are adjacent).  Writes the reordered queries and, for
- * each, its input position.  The sort key is the query's offset above the
- * tree's smallest key, clamped to the tree's key range (a monotone map, so
- * the order agrees with the key order); `sort_bits` leading bits of it are
- * used, rounded up to whole 8-bit passes (-1 = library choice, 0 = no
- * reordering: the queries are copied and the index is the identity).  The
- * sort is stable, so equal sort keys keep their input order.
+ * bt_sort_batch -- the first step of a search on its own: the on-device radix
+ * sort of the batch (Sec. IV-A: queries are sorted so that those routed to
+ * one node are adjacent).  Writes the reordered queries and, for each, its
+ * input position.  The sort key is the query's offset above the tree's
+ * smallest key, clamped to the tree's key range (a monotone map, so the
+ * order agrees with the key order), of which `sort_bits` leading bits are
+ * used (-1 = library choice, 0 = no reordering: the queries are copied and
+ * the index is the identity).  Two stages: a distribution of the batch on
+ * the leading D = min(sort_bits, 12, ceil(log2(nq / 4096))) bits, then a
+ * sort of every aligned run of 4096 positions on all `sort_bits` bits.  The
+ * result is ordered on the leading D bits across the batch and on the
+ * leading `sort_bits` bits within each aligned run of 4096 positions (for
+ * nq <= 4096: a sort on `sort_bits` bits).  The order of queries with equal
+ * sort keys is unspecified.
  *
  *   d_queries         nq keys (device).
  *   d_sorted_queries  nq keys (device), must not overlap d_queries.
@@ -190,17 +198,9 @@ bt_status bt_sort_batch(const bt_tree *tree, const void *d_queries, uint64_t nq,
                         void *d_sorted_queries, uint32_t *d_sorted_index, void *d_workspace,
                         uint64_t ws_bytes, bt_stream stream);
 
-/* Status of the last sort that ran in this workspace (bt_search_batch,
- * bt_search_batch_ex or bt_sort_batch with the same tree and nq): BT_OK, or
- * BT_ERR_TIMEOUT if a bounded wait of the sort's look-back gave up (the
- * results of that search are then invalid).  Synchronous: reads one word of
- * the workspace after the device has finished all work.  A search that did
- * not sort leaves the word as the previous sort left it. */
-bt_status bt_workspace_status(const bt_tree *tree, const void *d_workspace, uint64_t nq);
-
-/* Number of 8-bit radix passes bt_sort_batch / bt_search_batch would run
+/* Number of kernels the sort of bt_sort_batch / bt_search_batch launches
  * for this tree, batch size and sort_bits (0 = no sort).  -1 on a NULL tree. */
-int32_t bt_sort_passes(const bt_tree *tree, uint64_t nq, int32_t sort_bits);
+int32_t bt_sort_launches(const bt_tree *tree, uint64_t nq, int32_t sort_bits);
 
 /*
  * bt_descend_sorted -- the remaining steps on their own: the level-wise
@@ -251,7 +251,7 @@ bt_status bt_search_batch_host(const bt_tree *tree, const void *h_queries, uint6
  * critical request path that must not call cudaMalloc/cudaFree (they can
  * synchronize the whole device).
  *
- * Scratch space (sort buffers, histograms, look-back words) is a 2 MiB
+ * Scratch space (sort buffers, histograms, bucket cursors) is a 2 MiB
  * file-scope device array inside the library; every GPU that loads the
  * library holds it until the process exits.  The caller still passes the
  * queries and the outputs, as for bt_search_batch.
@@ -272,6 +272,215 @@ bt_status bt_search_batch_host(const bt_tree *tree, const void *h_queries, uint6
 #define BT_NOALLOC_MAX_QUERIES 65536
 bt_status bt_search_batch_noalloc(const bt_tree *tree, const void *d_queries, uint64_t nq,
                                   void *d_out_vals, uint8_t *d_out_found, bt_stream stream);
+
+/* ------------------------------------------------------------------------
+ * Many batches over several resident trees in one launch.  Not in the paper
+ * as such: it extends the paper's use of several kernel instances, each
+ * serving a share of the work (Sec. IV-G), to many small batches of uneven
+ * size addressed to different trees, served by one persistent launch.
+ * ------------------------------------------------------------------------ */
+
+/* One batch of a work list: `count` queries at d_queries[offset ..], whose
+ * results go to the same positions of the result arrays, searched in tree
+ * number `tree` of the forest. */
+typedef struct bt_batch_desc {
+    uint32_t tree;
+    uint32_t count;
+    uint64_t offset;
+} bt_batch_desc;
+
+typedef struct bt_forest bt_forest;
+
+/* A device table of `count` built trees with equal key and value widths
+ * (fanouts may differ).  The trees must outlive the forest. */
+bt_status bt_forest_create(const bt_tree *const *trees, uint32_t count, bt_forest **out);
+void bt_forest_free(bt_forest *forest);
+
+/* Device workspace for a work list of nbatches batches. */
+uint64_t bt_forest_workspace_bytes(uint32_t nbatches);
+
+/*
+ * bt_forest_search -- every batch of the device work list d_batches[0..n) in
+ * one persistent launch: 32-query chunks of all batches are shared out over
+ * resident warps; each chunk descends its tree level by level (each distinct
+ * node of the chunk staged once per level, Sec. IV-A) and writes value and
+ * found flag at its queries' positions.  Batches are not sorted (they are
+ * small; the per-warp distinct-node staging already reuses nodes).
+ *   warps_per_block  1..16, 0 = 8 (a tuning knob, see bt_autotune).
+ * Asynchronous, allocates nothing, may be captured in a CUDA graph.
+ * Errors: BT_ERR_ARG, BT_ERR_WORKSPACE, BT_ERR_CUDA.
+ */
+bt_status bt_forest_search(const bt_forest *forest, const bt_batch_desc *d_batches, uint32_t nbatches,
+                           const void *d_queries, void *d_out_vals, uint8_t *d_out_found, void *d_workspace,
+                           uint64_t ws_bytes, uint32_t warps_per_block, bt_stream stream);
+
+/* Launch parameters of a tree's single-tree searches. */
+typedef struct bt_tune {
+    uint32_t fanout;          /* m the tree was built with */
+    uint32_t warps_per_block; /* descent blocks: 4, 8 or 16 warps */
+    uint32_t pin_bytes;       /* budget for top levels kept in shared memory (0..49152) */
+    float us_per_batch;       /* median time of the sample batch with these settings */
+} bt_tune;
+
+/* Set the descent launch parameters of a built tree (not thread-safe with
+ * searches running on it).  BT_ERR_ARG on unsupported values. */
+bt_status bt_tree_set_launch(bt_tree *tree, uint32_t warps_per_block, uint32_t pin_bytes);
+
+/*
+ * bt_autotune -- build the tree at every fanout in {8, 16, 32, 64} and time
+ * a sample batch (d_sample, nsample device queries) through bt_search_batch
+ * for every combination of warps per block {4, 8, 16} and pinned bytes
+ * {0, 16384, 49152}; keep the fastest.  *out receives the tree built with
+ * the best fanout and launch parameters applied, *best the choice and its
+ * time.  Synchronizes `stream`.  Errors: as bt_build, plus BT_ERR_ARG.
+ */
+bt_status bt_autotune(const void *h_keys, const void *h_vals, uint64_t n, bt_width key_w, bt_width val_w,
+                      const void *d_sample, uint64_t nsample, bt_stream stream, bt_tree **out, bt_tune *best);
+
+/* ------------------------------------------------------------------------
+ * Serving: continuous batching of small lookup requests.  The paper times a
+ * host that writes a batch, runs the kernel and reads the results, and
+ * notes that a pipelined host overlaps its transfers with the kernel
+ * (Sec. V-B, Fig. 7).  A server keeps trees resident and serves requests
+ * from many callers: a worker thread coalesces waiting requests of one tree
+ * into a batch when the oldest has waited deadline_us or the batch is full,
+ * and runs it on a free slot (own stream, page-locked staging, device
+ * buffers, workspace): copy in, search, copy out.  Up to `slots` batches are
+ * in flight at once, so their work overlaps on the device while new requests
+ * are admitted into later batches as slots free up.  A batch is issued only
+ * while the staging bytes of all batches in flight stay within
+ * mem_cap_bytes; submissions beyond pending_cap_bytes of waiting requests
+ * are refused with BT_ERR_NOMEM (back-pressure).
+ * ------------------------------------------------------------------------ */
+typedef struct bt_server bt_server;
+
+typedef struct bt_server_opts {
+    uint32_t slots;             /* batches in flight at once, 1..64 */
+    uint32_t max_batch;         /* queries per batch, 1..2^24 (also the largest request) */
+    double deadline_us;         /* longest a request waits to be batched */
+    uint64_t mem_cap_bytes;     /* staging bytes of batches in flight (0 = unlimited) */
+    uint64_t pending_cap_bytes; /* bytes of waiting requests before refusal (0 = unlimited) */
+} bt_server_opts;
+
+typedef struct bt_server_stats {
+    uint64_t submitted, completed, lookups, batches;
+    uint32_t max_inflight;      /* most batches seen in flight at once */
+    float p50_us, p99_us, max_us; /* request latency, submission to results in place */
+} bt_server_stats;
+
+/* Start a server over `ntrees` resident trees (equal key and value widths).
+ * models: NULL, or one entry per tree, NULL or a model trained on that tree
+ * (its searches then use bt_learned_search_batch).  Trees and models must
+ * outlive the server.  Allocates the slots' buffers and starts the worker on
+ * the current device.  Errors: BT_ERR_ARG, BT_ERR_NOMEM, BT_ERR_CUDA. */
+bt_status bt_server_create(const bt_tree *const *trees, const bt_model *const *models, uint32_t ntrees,
+                           const bt_server_opts *opts, bt_server **out);
+
+/* Queue one request of `count` keys (host memory, read when its batch is
+ * formed) for tree number `tree`; the results are written to h_out_vals /
+ * h_out_found (host) before the request's ticket is reported done.  Buffers
+ * must stay valid until then.  Thread-safe.  BT_ERR_NOMEM: pending cap. */
+bt_status bt_server_submit(bt_server *server, uint32_t tree, const void *h_keys, uint32_t count,
+                           void *h_out_vals, uint8_t *h_out_found, uint64_t *ticket);
+
+/* Up to `max` tickets completed since the last poll. */
+bt_status bt_server_poll(bt_server *server, uint64_t *tickets, uint32_t max, uint32_t *n);
+
+/* Wait until every submitted request is complete (BT_ERR_TIMEOUT after timeout_s). */
+bt_status bt_server_drain(bt_server *server, double timeout_s);
+
+/* Counters and latency percentiles since creation or the last reset. */
+bt_status bt_server_get_stats(bt_server *server, bt_server_stats *out, int reset);
+
+/* Finish all accepted requests, stop the worker, free the slots. */
+void bt_server_destroy(bt_server *server);
+
+/* Load replay for measurements: submit request i at t_arrival_s[i] seconds
+ * after the call starts (tree[i], count[i] keys at h_keys[key_offset[i]..],
+ * results at the same offsets of h_out_vals / h_out_found), then drain.
+ * *wall_s receives the elapsed time. */
+bt_status bt_server_run_trace(bt_server *server, uint64_t n, const double *t_arrival_s, const uint32_t *tree,
+                              const uint32_t *count, const uint64_t *key_offset, const void *h_keys,
+                              void *h_out_vals, uint8_t *h_out_found, double *wall_s);
+
+/* ------------------------------------------------------------------------
+ * Learned leaf predictor.  Not in the paper: an extension in which a small
+ * fp32 model, fitted or trained on the GPU on the tree's own (stored key,
+ * leaf index) pairs, predicts a key's leaf directly so the search can skip
+ * the inner levels.  The model's maximum error over the stored keys -- the
+ * same device code computes it -- bounds a window of leaves around the
+ * prediction; the window's boundaries are checked with exact integer
+ * compares against the leaves' largest keys, and a warp any of whose queries
+ * is not proven to lie in its window takes the plain level-wise descent.
+ * Results are therefore always exactly those of bt_search_batch.
+ *
+ * Models (fp32 steps as listed; the CPU oracle reproduces the PL ones
+ * bit for bit):
+ *   BT_MODEL_PL  S segments split at key quantiles b_s = key of rank
+ *                floor(s*n/S); x = fp32(fp64(q - b_s)) * inv_w_s with
+ *                inv_w_s = fp32(1/fp64(b_{s+1} - b_s)) (the last width runs
+ *                one past the largest key); a least-squares line per segment
+ *                fitted in fp64 and stored in fp32; pred = fp32(fp32(slope_s *
+ *                x) + icpt_s), separately rounded.
+ *   BT_MODEL_MLP 1 -> 32 -> 32 -> 1 with ReLU on x = fp32(fp64(clamp(q) -
+ *                kmin)) * fp32(1/fp64(kmax - kmin)); trained with Adam on the
+ *                mean squared error against leaf / (L - 1); pred = output *
+ *                (L - 1).  Parameters (BT_MLP_PARAMS floats): W1[32], b1[32],
+ *                W2[32][32] (row = output unit), b2[32], w3[32], b3.
+ *   leaf_hat = rint(clamp(pred, 0, L - 1)).
+ * ------------------------------------------------------------------------ */
+#define BT_MLP_PARAMS 1153
+typedef enum bt_model_kind { BT_MODEL_PL = 1, BT_MODEL_MLP = 2 } bt_model_kind;
+
+typedef struct bt_learn_opts {
+    int32_t kind;          /* BT_MODEL_PL or BT_MODEL_MLP */
+    uint32_t segments;     /* PL: S, 1..65536 (capped at n) */
+    const float *h_init;   /* MLP: BT_MLP_PARAMS initial parameters (host, read only) */
+    uint32_t steps;        /* MLP: Adam steps (>= 1) */
+    uint32_t batch;        /* MLP: samples per step, 1..2^22, ranks drawn by splitmix64 */
+    float lr;              /* MLP: Adam learning rate (> 0) */
+    uint64_t seed;         /* MLP: sampling seed */
+} bt_learn_opts;
+
+typedef struct bt_model_info {
+    int32_t kind;
+    uint32_t segments;     /* PL: S actually used */
+    uint32_t leaves;       /* L of the tree it was trained on */
+    uint32_t max_err;      /* max |leaf_hat - leaf| over every stored key */
+    float final_loss;      /* MLP: mean squared error of the last training step */
+    uint64_t device_bytes; /* device memory held by the model */
+} bt_model_info;
+
+/* Fit (PL) or train (MLP) a model for `tree` on the GPU and compute its
+ * error bound; synchronizes `stream`.  The model is only valid with this tree.
+ * Errors: BT_ERR_ARG (empty tree, bad options), BT_ERR_NOMEM, BT_ERR_CUDA. */
+bt_status bt_model_train(const bt_tree *tree, const bt_learn_opts *opts, bt_stream stream, bt_model **out);
+void bt_model_free(bt_model *model);
+bt_status bt_model_get_info(const bt_model *model, bt_model_info *out);
+/* Copy the parameters to host memory (synchronous).  PL: b[S] (uint64),
+ * inv_w[S], slope[S], icpt[S] (float), 20*S bytes; MLP: BT_MLP_PARAMS
+ * floats.  BT_ERR_ARG if `bytes` is too small. */
+bt_status bt_model_copy_params(const bt_model *model, void *h_dst, uint64_t bytes);
+
+/* Mean-squared-error gradient of an MLP over n given samples, the training
+ * kernel's own forward and backward pass: writes d_grad[BT_MLP_PARAMS] and
+ * d_loss[0] = mean((f(x_i) - t_i)^2).  d_params, d_x, d_t, d_grad, d_loss are
+ * device float arrays.  Asynchronous on `stream`. */
+bt_status bt_mlp_grad(const float *d_params, const float *d_x, const float *d_t, uint32_t n,
+                      float *d_grad, float *d_loss, bt_stream stream);
+
+/* bt_descend_sorted with the model: same arguments and results, plus
+ * d_stats (NULL or 2 device counters): warps that the model window served,
+ * warps that fell back to the plain descent. */
+bt_status bt_learned_descend_sorted(const bt_tree *tree, const bt_model *model, const void *d_queries,
+                                    const uint32_t *d_index, uint64_t nq, void *d_out_vals,
+                                    uint8_t *d_out_found, unsigned long long *d_stats, bt_stream stream);
+
+/* bt_search_batch with the model (sort, then the learned descent); same
+ * workspace, results identical to bt_search_batch. */
+bt_status bt_learned_search_batch(const bt_tree *tree, const bt_model *model, const void *d_queries,
+                                  uint64_t nq, void *d_out_vals, uint8_t *d_out_found, void *d_workspace,
+                                  uint64_t ws_bytes, bt_stream stream);
 
 /* Static text for a status code. */
 const char *bt_status_str(bt_status status);

@@ -31,9 +31,14 @@ STATUS = {0: "BT_OK", 1: "BT_ERR_ARG", 2: "BT_ERR_UNSORTED", 3: "BT_ERR_DUPLICAT
 
 # Every symbol include/btree_gb300.h declares.
 EXPORTED = ("bt_build", "bt_free", "bt_tree_info", "bt_tree_copy_image", "bt_search_workspace_bytes",
-            "bt_search_batch", "bt_search_batch_ex", "bt_sort_batch", "bt_descend_sorted", "bt_sort_passes", "bt_workspace_status",
+            "bt_search_batch", "bt_search_batch_ex", "bt_sort_batch", "bt_descend_sorted", "bt_sort_launches",
             "bt_search_host_workspace_bytes",
-            "bt_search_batch_host", "bt_search_batch_noalloc", "bt_status_str", "bt_last_error_detail")
+            "bt_search_batch_host", "bt_search_batch_noalloc", "bt_status_str", "bt_last_error_detail",
+            "bt_model_train", "bt_model_free", "bt_model_get_info", "bt_model_copy_params", "bt_mlp_grad",
+            "bt_learned_descend_sorted", "bt_learned_search_batch", "bt_forest_create", "bt_forest_free",
+            "bt_forest_workspace_bytes", "bt_forest_search", "bt_tree_set_launch", "bt_autotune",
+            "bt_server_create", "bt_server_submit", "bt_server_poll", "bt_server_drain", "bt_server_get_stats",
+            "bt_server_destroy", "bt_server_run_trace")
 
 
 class bt_info(ctypes.Structure):
@@ -69,10 +74,8 @@ _lib.bt_search_batch_ex.restype = _i
 _lib.bt_search_batch_ex.argtypes = [_vp, _vp, _u64, _vp, _vp, _vp, _u64, ctypes.POINTER(bt_search_opts), _vp]
 _lib.bt_sort_batch.restype = _i
 _lib.bt_sort_batch.argtypes = [_vp, _vp, _u64, ctypes.c_int32, _vp, _vp, _vp, _u64, _vp]
-_lib.bt_sort_passes.restype = ctypes.c_int32
-_lib.bt_sort_passes.argtypes = [_vp, _u64, ctypes.c_int32]
-_lib.bt_workspace_status.restype = _i
-_lib.bt_workspace_status.argtypes = [_vp, _vp, _u64]
+_lib.bt_sort_launches.restype = ctypes.c_int32
+_lib.bt_sort_launches.argtypes = [_vp, _u64, ctypes.c_int32]
 _lib.bt_descend_sorted.restype = _i
 _lib.bt_descend_sorted.argtypes = [_vp, _vp, _vp, _u64, _vp, _vp, _vp, _vp]
 _lib.bt_search_batch_host.restype = _i
@@ -194,16 +197,8 @@ def bt_sort_batch(tree: int, d_queries, nq: int, sort_bits: int, d_sorted_querie
     _check("bt_sort_batch", st)
 
 
-def bt_sort_passes(tree: int, nq: int, sort_bits: int = -1) -> int:
-    return int(_lib.bt_sort_passes(tree, nq, sort_bits))
-
-
-def bt_workspace_status(tree: int, d_workspace, nq: int) -> int:
-    """0 (BT_OK) or 7 (BT_ERR_TIMEOUT) for the last sort in this workspace."""
-    st = int(_lib.bt_workspace_status(tree, _dptr(d_workspace), nq))
-    if st not in (0, 7):
-        _check("bt_workspace_status", st)
-    return st
+def bt_sort_launches(tree: int, nq: int, sort_bits: int = -1) -> int:
+    return int(_lib.bt_sort_launches(tree, nq, sort_bits))
 
 
 def bt_descend_sorted(tree: int, d_queries, d_index, nq: int, d_out_vals, d_out_found,
@@ -229,6 +224,246 @@ def bt_search_batch_host(tree: int, h_queries, nq: int, h_out_vals, h_out_found,
     _check("bt_search_batch_host", st)
 
 
+BT_MODEL_PL, BT_MODEL_MLP = 1, 2
+BT_MLP_PARAMS = 1153
+
+
+class bt_learn_opts(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("segments", ctypes.c_uint32), ("h_init", ctypes.c_void_p),
+                ("steps", ctypes.c_uint32), ("batch", ctypes.c_uint32), ("lr", ctypes.c_float),
+                ("seed", ctypes.c_uint64)]
+
+
+class bt_model_info(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("segments", ctypes.c_uint32), ("leaves", ctypes.c_uint32),
+                ("max_err", ctypes.c_uint32), ("final_loss", ctypes.c_float), ("device_bytes", ctypes.c_uint64)]
+
+
+_lib.bt_model_train.restype = _i
+_lib.bt_model_train.argtypes = [_vp, ctypes.POINTER(bt_learn_opts), _vp, ctypes.POINTER(_vp)]
+_lib.bt_model_free.restype = None
+_lib.bt_model_free.argtypes = [_vp]
+_lib.bt_model_get_info.restype = _i
+_lib.bt_model_get_info.argtypes = [_vp, ctypes.POINTER(bt_model_info)]
+_lib.bt_model_copy_params.restype = _i
+_lib.bt_model_copy_params.argtypes = [_vp, _vp, _u64]
+_lib.bt_mlp_grad.restype = _i
+_lib.bt_mlp_grad.argtypes = [_vp, _vp, _vp, ctypes.c_uint32, _vp, _vp, _vp]
+_lib.bt_learned_descend_sorted.restype = _i
+_lib.bt_learned_descend_sorted.argtypes = [_vp, _vp, _vp, _vp, _u64, _vp, _vp, _vp, _vp]
+_lib.bt_learned_search_batch.restype = _i
+_lib.bt_learned_search_batch.argtypes = [_vp, _vp, _vp, _u64, _vp, _vp, _vp, _u64, _vp]
+
+
+def bt_model_train(tree: int, kind: int, segments: int = 256, h_init=None, steps: int = 0, batch: int = 0,
+                   lr: float = 0.0, seed: int = 0, stream=None) -> int:
+    """Fit (PL) or train (MLP) a leaf predictor for `tree` on the GPU."""
+    init = None
+    if h_init is not None:
+        init = np.ascontiguousarray(h_init, dtype=np.float32)
+        if init.size != BT_MLP_PARAMS:
+            raise ValueError(f"h_init must hold {BT_MLP_PARAMS} floats")
+    o = bt_learn_opts(kind, segments, init.ctypes.data if init is not None else None, steps, batch, lr, seed)
+    out = _vp()
+    _check("bt_model_train", _lib.bt_model_train(tree, ctypes.byref(o), _stream_handle(stream), ctypes.byref(out)))
+    return out.value
+
+
+def bt_model_free(model: int) -> None:
+    _lib.bt_model_free(model)
+
+
+def bt_model_get_info(model: int) -> bt_model_info:
+    info = bt_model_info()
+    _check("bt_model_get_info", _lib.bt_model_get_info(model, ctypes.byref(info)))
+    return info
+
+
+def bt_model_copy_params(model: int):
+    """PL: (b uint64[S], inv_w, slope, icpt float32[S]); MLP: float32[1153]."""
+    info = bt_model_get_info(model)
+    if info.kind == BT_MODEL_PL:
+        S = int(info.segments)
+        buf = np.empty(20 * S, np.uint8)
+        _check("bt_model_copy_params", _lib.bt_model_copy_params(model, buf.ctypes.data, buf.size))
+        return (buf[:8 * S].view(np.uint64).copy(), buf[8 * S:12 * S].view(np.float32).copy(),
+                buf[12 * S:16 * S].view(np.float32).copy(), buf[16 * S:].view(np.float32).copy())
+    out = np.empty(BT_MLP_PARAMS, np.float32)
+    _check("bt_model_copy_params", _lib.bt_model_copy_params(model, out.ctypes.data, out.nbytes))
+    return out
+
+
+def bt_mlp_grad(d_params, d_x, d_t, n: int, d_grad, d_loss, stream=None) -> None:
+    _check("bt_mlp_grad", _lib.bt_mlp_grad(_dptr(d_params), _dptr(d_x), _dptr(d_t), n, _dptr(d_grad),
+                                           _dptr(d_loss), _stream_handle(stream)))
+
+
+def bt_learned_descend_sorted(tree: int, model: int, d_queries, d_index, nq: int, d_out_vals, d_out_found,
+                              d_stats=None, stream=None) -> None:
+    st = _lib.bt_learned_descend_sorted(tree, model, _dptr(d_queries), _dptr(d_index), nq, _dptr(d_out_vals),
+                                        _dptr(d_out_found), _dptr(d_stats), _stream_handle(stream))
+    _check("bt_learned_descend_sorted", st)
+
+
+def bt_learned_search_batch(tree: int, model: int, d_queries, nq: int, d_out_vals, d_out_found, d_workspace,
+                            ws_bytes: int, stream=None) -> None:
+    st = _lib.bt_learned_search_batch(tree, model, _dptr(d_queries), nq, _dptr(d_out_vals), _dptr(d_out_found),
+                                      _dptr(d_workspace), ws_bytes, _stream_handle(stream))
+    _check("bt_learned_search_batch", st)
+
+
+class bt_batch_desc(ctypes.Structure):
+    _fields_ = [("tree", ctypes.c_uint32), ("count", ctypes.c_uint32), ("offset", ctypes.c_uint64)]
+
+
+class bt_tune(ctypes.Structure):
+    _fields_ = [("fanout", ctypes.c_uint32), ("warps_per_block", ctypes.c_uint32), ("pin_bytes", ctypes.c_uint32),
+                ("us_per_batch", ctypes.c_float)]
+
+
+BATCH_DESC_DTYPE = np.dtype([("tree", np.uint32), ("count", np.uint32), ("offset", np.uint64)])
+
+_lib.bt_forest_create.restype = _i
+_lib.bt_forest_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_uint32, ctypes.POINTER(_vp)]
+_lib.bt_forest_free.restype = None
+_lib.bt_forest_free.argtypes = [_vp]
+_lib.bt_forest_workspace_bytes.restype = _u64
+_lib.bt_forest_workspace_bytes.argtypes = [ctypes.c_uint32]
+_lib.bt_forest_search.restype = _i
+_lib.bt_forest_search.argtypes = [_vp, _vp, ctypes.c_uint32, _vp, _vp, _vp, _vp, _u64, ctypes.c_uint32, _vp]
+_lib.bt_tree_set_launch.restype = _i
+_lib.bt_tree_set_launch.argtypes = [_vp, ctypes.c_uint32, ctypes.c_uint32]
+_lib.bt_autotune.restype = _i
+_lib.bt_autotune.argtypes = [_vp, _vp, _u64, _i, _i, _vp, _u64, _vp, ctypes.POINTER(_vp), ctypes.POINTER(bt_tune)]
+
+
+def bt_forest_create(trees) -> int:
+    arr = (_vp * len(trees))(*[t if isinstance(t, int) else t.handle for t in trees])
+    out = _vp()
+    _check("bt_forest_create", _lib.bt_forest_create(arr, len(trees), ctypes.byref(out)))
+    return out.value
+
+
+def bt_forest_free(forest: int) -> None:
+    _lib.bt_forest_free(forest)
+
+
+def bt_forest_workspace_bytes(nbatches: int) -> int:
+    return int(_lib.bt_forest_workspace_bytes(nbatches))
+
+
+def bt_forest_search(forest: int, d_batches, nbatches: int, d_queries, d_out_vals, d_out_found, d_workspace,
+                     ws_bytes: int, warps_per_block: int = 0, stream=None) -> None:
+    st = _lib.bt_forest_search(forest, _dptr(d_batches), nbatches, _dptr(d_queries), _dptr(d_out_vals),
+                               _dptr(d_out_found), _dptr(d_workspace), ws_bytes, warps_per_block,
+                               _stream_handle(stream))
+    _check("bt_forest_search", st)
+
+
+def bt_tree_set_launch(tree: int, warps_per_block: int, pin_bytes: int) -> None:
+    _check("bt_tree_set_launch", _lib.bt_tree_set_launch(tree, warps_per_block, pin_bytes))
+
+
+def bt_autotune(h_keys: np.ndarray, h_vals: np.ndarray, d_sample, nsample: int, stream=None):
+    """(tree handle, bt_tune) with the fastest fanout and launch settings."""
+    k = np.ascontiguousarray(h_keys)
+    v = np.ascontiguousarray(h_vals)
+    out = _vp()
+    best = bt_tune()
+    st = _lib.bt_autotune(k.ctypes.data, v.ctypes.data, k.size, _width(k.dtype), _width(v.dtype), _dptr(d_sample),
+                          nsample, _stream_handle(stream), ctypes.byref(out), ctypes.byref(best))
+    _check("bt_autotune", st)
+    return out.value, best
+
+
+class bt_server_opts(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_uint32), ("max_batch", ctypes.c_uint32), ("deadline_us", ctypes.c_double),
+                ("mem_cap_bytes", ctypes.c_uint64), ("pending_cap_bytes", ctypes.c_uint64)]
+
+
+class bt_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("lookups", ctypes.c_uint64),
+                ("batches", ctypes.c_uint64), ("max_inflight", ctypes.c_uint32), ("p50_us", ctypes.c_float),
+                ("p99_us", ctypes.c_float), ("max_us", ctypes.c_float)]
+
+
+_lib.bt_server_create.restype = _i
+_lib.bt_server_create.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_uint32,
+                                  ctypes.POINTER(bt_server_opts), ctypes.POINTER(_vp)]
+_lib.bt_server_submit.restype = _i
+_lib.bt_server_submit.argtypes = [_vp, ctypes.c_uint32, _vp, ctypes.c_uint32, _vp, _vp, ctypes.POINTER(_u64)]
+_lib.bt_server_poll.restype = _i
+_lib.bt_server_poll.argtypes = [_vp, ctypes.POINTER(_u64), ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]
+_lib.bt_server_drain.restype = _i
+_lib.bt_server_drain.argtypes = [_vp, ctypes.c_double]
+_lib.bt_server_get_stats.restype = _i
+_lib.bt_server_get_stats.argtypes = [_vp, ctypes.POINTER(bt_server_stats), _i]
+_lib.bt_server_destroy.restype = None
+_lib.bt_server_destroy.argtypes = [_vp]
+_lib.bt_server_run_trace.restype = _i
+_lib.bt_server_run_trace.argtypes = [_vp, _u64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_double)]
+
+
+def bt_server_create(trees, models=None, slots: int = 4, max_batch: int = 4096, deadline_us: float = 50.0,
+                     mem_cap_bytes: int = 0, pending_cap_bytes: int = 0) -> int:
+    n = len(trees)
+    t_arr = (_vp * n)(*[t if isinstance(t, int) else t.handle for t in trees])
+    m_arr = None
+    if models is not None:
+        m_arr = (_vp * n)(*[m for m in models])
+    o = bt_server_opts(slots, max_batch, deadline_us, mem_cap_bytes, pending_cap_bytes)
+    out = _vp()
+    _check("bt_server_create", _lib.bt_server_create(t_arr, m_arr, n, ctypes.byref(o), ctypes.byref(out)))
+    return out.value
+
+
+def bt_server_submit(server: int, tree: int, h_keys: np.ndarray, h_out_vals: np.ndarray,
+                     h_out_found: np.ndarray) -> int:
+    """Queue a request; the numpy buffers must stay alive until it completes."""
+    t = _u64()
+    st = _lib.bt_server_submit(server, tree, h_keys.ctypes.data, h_keys.size, h_out_vals.ctypes.data,
+                               h_out_found.ctypes.data, ctypes.byref(t))
+    _check("bt_server_submit", st)
+    return int(t.value)
+
+
+def bt_server_poll(server: int, max_tickets: int = 4096):
+    buf = (_u64 * max_tickets)()
+    n = ctypes.c_uint32()
+    _check("bt_server_poll", _lib.bt_server_poll(server, buf, max_tickets, ctypes.byref(n)))
+    return [int(buf[i]) for i in range(n.value)]
+
+
+def bt_server_drain(server: int, timeout_s: float = 60.0) -> None:
+    _check("bt_server_drain", _lib.bt_server_drain(server, timeout_s))
+
+
+def bt_server_get_stats(server: int, reset: bool = False) -> bt_server_stats:
+    s = bt_server_stats()
+    _check("bt_server_get_stats", _lib.bt_server_get_stats(server, ctypes.byref(s), int(reset)))
+    return s
+
+
+def bt_server_destroy(server: int) -> None:
+    _lib.bt_server_destroy(server)
+
+
+def bt_server_run_trace(server: int, t_arrival_s: np.ndarray, tree: np.ndarray, count: np.ndarray,
+                        key_offset: np.ndarray, h_keys: np.ndarray, h_out_vals: np.ndarray,
+                        h_out_found: np.ndarray) -> float:
+    """Replay an arrival trace through the server; returns the wall time (s)."""
+    ta = np.ascontiguousarray(t_arrival_s, np.float64)
+    tr = np.ascontiguousarray(tree, np.uint32)
+    ct = np.ascontiguousarray(count, np.uint32)
+    ko = np.ascontiguousarray(key_offset, np.uint64)
+    wall = ctypes.c_double()
+    st = _lib.bt_server_run_trace(server, ta.size, ta.ctypes.data, tr.ctypes.data, ct.ctypes.data, ko.ctypes.data,
+                                  h_keys.ctypes.data, h_out_vals.ctypes.data, h_out_found.ctypes.data,
+                                  ctypes.byref(wall))
+    _check("bt_server_run_trace", st)
+    return float(wall.value)
+
+
 BT_NOALLOC_MAX_QUERIES = 65536
 
 
@@ -250,8 +485,10 @@ def _torch_dtype(width: int):
 class BTree:
     """A tree on the current CUDA device with convenience search methods."""
 
-    def __init__(self, keys: np.ndarray, vals: np.ndarray, fanout: int, stream=None):
-        self.handle = bt_build(keys, vals, fanout, stream)
+    def __init__(self, keys: np.ndarray | None, vals: np.ndarray | None, fanout: int = 0, stream=None,
+                 handle: int | None = None):
+        """Build from sorted keys/values, or take ownership of a built tree's handle."""
+        self.handle = handle if handle is not None else bt_build(keys, vals, fanout, stream)
         i = bt_tree_info(self.handle)
         self.height = int(i.height)
         self.fanout = int(i.fanout)

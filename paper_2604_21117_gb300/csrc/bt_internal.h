@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include "btree_gb300.h"
+#include "learned.cuh"
 
 namespace btgb {
 
@@ -30,7 +31,11 @@ struct DevTree {
     int key_bytes, val_bytes;
     int pin_levels;      // top levels copied to shared memory by the descent
     uint32_t pin_bytes;  // bytes from the root's block to the end of those levels
+    int warps;           // warps per descent block
 };
+
+// Whole top levels (never the leaves) whose bytes fit `budget`, root first.
+void set_pin_levels(DevTree &d, const bt_info &info, uint32_t budget);
 
 }  // namespace btgb
 
@@ -38,6 +43,12 @@ struct bt_tree {
     btgb::DevTree dev;
     bt_info info;
     void *d_image;
+};
+
+struct bt_model {
+    btgb::ModelDev dev;
+    bt_model_info info;
+    void *d_mem;
 };
 
 namespace btgb {

@@ -38,9 +38,29 @@ static inline void store_uint(void *p, uint64_t i, int bytes, uint64_t v)
 
 static inline uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
 
+void set_pin_levels(DevTree &d, const bt_info &info, uint32_t budget)
+{
+    d.pin_levels = 0;
+    d.pin_bytes = 0;
+    for (int l = 0; l + 1 < d.height; ++l) {
+        const uint64_t end = info.level_key_offset[l] + d.nodes[l] * static_cast<uint64_t>(d.m) * d.key_bytes;
+        if (end > budget) break;
+        d.pin_levels = l + 1;
+        d.pin_bytes = static_cast<uint32_t>((end + 15) / 16 * 16);
+    }
+}
+
 }  // namespace btgb
 
 using namespace btgb;
+
+extern "C" bt_status bt_tree_set_launch(bt_tree *t, uint32_t warps_per_block, uint32_t pin_bytes)
+{
+    if (!t || warps_per_block < 1 || warps_per_block > 16 || pin_bytes > 49152) return BT_ERR_ARG;
+    t->dev.warps = static_cast<int>(warps_per_block);
+    set_pin_levels(t->dev, t->info, pin_bytes);
+    return BT_OK;
+}
 
 extern "C" const char *bt_last_error_detail(void) { return g_detail; }
 
@@ -123,14 +143,10 @@ extern "C" bt_status bt_build(const void *h_keys, const void *h_vals, uint64_t n
     if (h > 0) off = align_up(off + up[0] * m * vb, 256);
     t->info.device_bytes = off;
 
-    // Top levels small enough for the descent to keep in shared memory
-    // (whole levels, root first, never the leaves; 16 KB at most).
-    for (int l = 0; l + 1 < h; ++l) {
-        const uint64_t end = t->info.level_key_offset[l] + d.nodes[l] * m * kb;
-        if (end > 16384) break;
-        d.pin_levels = l + 1;
-        d.pin_bytes = static_cast<uint32_t>((end + 15) / 16 * 16);
-    }
+    // Descent launch defaults: 8 warps per block, top levels up to 16 KB
+    // kept in shared memory (bt_tree_set_launch / bt_autotune change them).
+    d.warps = 8;
+    set_pin_levels(d, t->info, 16384);
 
     // Shape arithmetic: children (or keys, for leaves) per node.
     for (int l = 0; l < h; ++l) {

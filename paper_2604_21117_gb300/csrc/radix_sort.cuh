@@ -1,25 +1,32 @@
-// On-device stable LSD radix sort of (query, input position) pairs.
+// On-device radix sort of (query, input position) pairs.
 //
 // The paper sorts the query batch so that all queries routed to one node
 // are adjacent and served by one node fetch (Sec. IV-A, Sec. IV-E).  Here
 // the sort key is the query's normalised offset above the tree's smallest
-// key (see SortNorm), 8 bits per pass, least significant digit first.
+// key (see SortNorm); what the descent needs is that each run of 32
+// consecutive queries covers a narrow key range, which this two-stage radix
+// sort gives at the cost of one global distribution:
 //
-// Single-pass ("onesweep") organisation, one kernel per digit pass plus one
-// histogram kernel for all passes:
-//   k_sort_hist      global digit histograms of every pass (one read);
-//   k_sort_pass      per tile of kSortTile elements: stable local ranking
-//                    (warp match + per-warp counters), publication of the
-//                    tile's per-digit counts, decoupled look-back over the
-//                    preceding tiles for the digit offsets (Merrill & Garland,
-//                    "Single-pass Parallel Prefix Scan with Decoupled
-//                    Look-back", 2016), a local reorder in shared memory and
-//                    coalesced runs of writes.
-// Tiles are claimed in order from an atomic counter, so a tile only ever
-// waits on tiles whose blocks are already running.  Every wait is bounded:
-// after kLookbackSpinLimit polls the block records BT_ERR_TIMEOUT in the
-// workspace error word and carries on (the output is then wrong, and the
-// error is reported by bt_workspace_status).
+//   1. MSD distribution on the leading D bits (D = 0..12, about nq/4096
+//      buckets, at most 2^20 (bucket, tile) pairs), counting sort style:
+//        k_msd_hist     per-tile bucket histograms into a [bucket][tile]
+//                       matrix (no atomics);
+//        k_msd_offsets  one block: the matrix read bucket-major becomes the
+//                       exclusive start of every (bucket, tile) run;
+//        k_msd_scatter  per tile: the elements are regrouped by bucket in
+//                       shared memory and written as contiguous runs at
+//                       their (bucket, tile) starts.
+//      No block waits on another (no look-back, no grid barrier).  Runs
+//      keep tile order inside a bucket; inside a tile the order of one
+//      bucket's elements is that of shared-memory atomics (unspecified).
+//   2. k_local_sort: every aligned run of kSortTile positions is sorted
+//      in shared memory by the leading `bits` bits (D bucket bits first),
+//      stable LSD passes of 8 bits with warp multisplit ranking.
+//
+// Result: ordered on the leading D bits across the batch, and on the
+// leading `bits` bits within every aligned run of kSortTile positions.
+// Batches of at most kSortTile queries need only stage 2: a full sort on
+// `bits` bits in one launch.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -31,20 +38,21 @@ namespace btgb {
 struct SortNorm {
     uint64_t kmin;
     uint64_t range;
-    int shift;
-    int passes;
+    int rl;        // bit length of the key range
+    int bits;      // leading bits ordered within a tile
+    int dbits;     // leading bits of the global distribution (0 = none)
 };
 
-// Normalised sort digit of a query: its offset above the smallest key,
-// clamped to the key range, shifted so the used leading bits remain.
-// Monotone in the query, so ordering by it agrees with the key order.
+// Leading `nbits` bits of the normalised key: the offset above the smallest
+// key, clamped to the key range, as a number with rl bits.  Monotone in q.
 template <typename K>
-__device__ __forceinline__ uint32_t sort_digit(K q, const SortNorm &s, int pass)
+__device__ __forceinline__ uint64_t sort_field(K q, const SortNorm &s, int nbits)
 {
     const uint64_t x = static_cast<uint64_t>(q);
     uint64_t nk = (x <= s.kmin) ? 0 : x - s.kmin;
     if (nk > s.range) nk = s.range;
-    return static_cast<uint32_t>((nk >> (s.shift + 8 * pass)) & 0xFFu);
+    const int sh = s.rl > nbits ? s.rl - nbits : 0;
+    return nbits == 0 ? 0ull : (nk >> sh);
 }
 
 __device__ __forceinline__ unsigned sort_lanemask_lt()
@@ -58,20 +66,16 @@ constexpr int kSortTile = 4096;
 constexpr int kSortThreads = 512;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortPerWarp = kSortTile / kSortWarps;  // 256 = 8 rounds of 32
-constexpr int kMaxPasses = 8;
-constexpr uint64_t kFlagAgg = 1ull << 62;
-constexpr uint64_t kFlagIncl = 2ull << 62;
-constexpr uint32_t kLookbackSpinLimit = 1u << 24;  // with a 64 ns back-off: about a second
-constexpr int kLookbackWindow = 16;
+constexpr int kMaxDistBits = 12;
+constexpr int kMaxBuckets = 1 << kMaxDistBits;
+constexpr uint64_t kMaxBucketTiles = 1ull << 20;  // cap on (bucket, tile) pairs
 
-// Lanes (within `valid`) whose 8-bit digit equals this lane's: the warp
-// multisplit by eight ballots, one per digit bit.  Every lane of the warp
-// must call it.
-__device__ __forceinline__ unsigned warp_match8(uint32_t d, unsigned valid)
+// Lanes (within `valid`) whose `nbits`-bit digit equals this lane's: the
+// warp multisplit by one ballot per digit bit.  Every lane must call it.
+__device__ __forceinline__ unsigned warp_match_bits(uint32_t d, unsigned valid, int nbits)
 {
     unsigned same = valid;
-#pragma unroll
-    for (int b = 0; b < 8; ++b) {
+    for (int b = 0; b < nbits; ++b) {
         const bool bit = (d >> b) & 1u;
         const unsigned bal = __ballot_sync(0xffffffffu, bit);
         same &= bit ? bal : ~bal;
@@ -79,27 +83,47 @@ __device__ __forceinline__ unsigned warp_match8(uint32_t d, unsigned valid)
     return same;
 }
 
-// Workspace block used by the sort besides the ping-pong buffers:
-//   ghist[kMaxPasses][256] u32 | tile_ctr[kMaxPasses] u32 | err u32 | status
-struct SortMeta {
-    uint32_t *ghist;
-    uint32_t *tile_ctr;
-    uint32_t *err;
-    unsigned long long *status;  // [passes][ntiles][256]
-};
-
-template <typename K>
-__global__ void __launch_bounds__(kSortThreads) k_sort_hist(const K *__restrict__ q, uint64_t nq,
-                                                            SortNorm sn, uint32_t *__restrict__ ghist)
+// Block-wide exclusive scan of one value per thread; `tmp` holds 32 words.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *tmp)
 {
-    __shared__ uint32_t h[kMaxPasses][256];
-    for (int i = threadIdx.x; i < kMaxPasses * 256; i += blockDim.x) (&h[0][0])[i] = 0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) tmp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < nw ? tmp[lane] : 0u;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        tmp[lane] = w;  // inclusive warp totals
+    }
+    __syncthreads();
+    const uint32_t r = x - v + (warp > 0 ? tmp[warp - 1] : 0u);
+    __syncthreads();
+    return r;
+}
+
+// ------------------------------------------------------ 1. distribution
+
+// Per-tile bucket histogram, written to counts[bucket * ntiles + tile].
+template <typename K>
+__global__ void __launch_bounds__(kSortThreads) k_msd_hist(const K *__restrict__ q, uint64_t nq, SortNorm sn,
+                                                           uint32_t *__restrict__ counts, uint32_t ntiles)
+{
+    __shared__ uint32_t h[kMaxBuckets];
+    const int nb = 1 << sn.dbits;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) h[i] = 0;
     __syncthreads();
     constexpr int R = kSortTile / kSortThreads;
     const uint64_t base = static_cast<uint64_t>(blockIdx.x) * kSortTile;
     K key[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) {  // all loads in flight before any use
+    for (int r = 0; r < R; ++r) {
         const uint64_t pos = base + r * kSortThreads + threadIdx.x;
         if (pos < nq) key[r] = q[pos];
     }
@@ -108,202 +132,244 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const K *__restrict_
         const uint64_t pos = base + r * kSortThreads + threadIdx.x;
         const bool valid = pos < nq;
         const unsigned vm = __ballot_sync(0xffffffffu, valid);
-        for (int p = 0; p < sn.passes; ++p) {
-            const uint32_t d = valid ? sort_digit(key[r], sn, p) : 0u;
-            const unsigned same = warp_match8(d, vm);
-            if (valid && (same & sort_lanemask_lt()) == 0) atomicAdd(&h[p][d], __popc(same));
+        const uint32_t d = valid ? static_cast<uint32_t>(sort_field(key[r], sn, sn.dbits)) : 0u;
+        const unsigned same = warp_match_bits(d, vm, sn.dbits);
+        if (valid && (same & sort_lanemask_lt()) == 0) atomicAdd(&h[d], __popc(same));
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) counts[static_cast<uint64_t>(i) * ntiles + blockIdx.x] = h[i];
+}
+
+// One block: the [bucket][tile] count matrix, read bucket-major, becomes the
+// exclusive offsets of every (bucket, tile) run.  Each warp owns a
+// contiguous segment: it sums it, the warp sums are scanned, then the warp
+// walks its segment in rows of 32 (8 rows loaded ahead), scanning each row.
+__global__ void __launch_bounds__(1024) k_msd_offsets(uint32_t *__restrict__ counts, uint32_t total)
+{
+    __shared__ uint32_t tmp[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint32_t seg = ((total + nw - 1) / nw + 31) / 32 * 32;
+    const uint32_t lo = warp * seg < total ? warp * seg : total;
+    const uint32_t hi = lo + seg < total ? lo + seg : total;
+    uint32_t sum = 0;
+    for (uint32_t i = lo + lane; i < hi; i += 32) sum += counts[i];
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) tmp[warp] = sum;
+    __syncthreads();
+    uint32_t run = 0;
+    for (int w = 0; w < warp; ++w) run += tmp[w];
+    constexpr int kAhead = 8;
+    for (uint32_t r0 = lo; r0 < hi; r0 += 32 * kAhead) {
+        uint32_t v[kAhead];
+#pragma unroll
+        for (int k = 0; k < kAhead; ++k) {
+            const uint32_t i = r0 + 32 * k + lane;
+            v[k] = i < hi ? counts[i] : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < kAhead; ++k) {
+            uint32_t x = v[k];
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            const uint32_t i = r0 + 32 * k + lane;
+            if (i < hi) counts[i] = run + x - v[k];
+            run += __shfl_sync(0xffffffffu, x, 31);
         }
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < sn.passes * 256; i += blockDim.x) {
-        const uint32_t v = (&h[0][0])[i];
-        if (v) atomicAdd(ghist + i, v);
-    }
-}
-
-__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v)
-{
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
-__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p)
-{
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// Exclusive scan of 256 values held one per thread by threads 0..255;
-// all threads of the block must call it.  `tmp` holds 8 words.
-__device__ __forceinline__ uint32_t block_excl_scan256(uint32_t v, uint32_t *tmp)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t x = v;
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (warp < 8 && lane == 31) tmp[warp] = x;
-    __syncthreads();
-    uint32_t before = 0;
-    if (warp < 8)
-        for (int w = 0; w < warp; ++w) before += tmp[w];
-    __syncthreads();
-    return before + x - v;
 }
 
 template <typename K>
-struct SortPassSmem {
-    uint32_t wh[kSortWarps][256];
-    uint32_t tstart[256];
-    uint32_t gbase[256];
-    uint32_t tpref[256];
-    uint32_t scan_tmp[8];
-    uint32_t tile;
+struct MsdSmem {
+    uint32_t cnt[kMaxBuckets];    // tile bucket counts, then local starts
+    uint32_t base[kMaxBuckets];   // reserved global start of the tile's run per bucket
+    uint32_t scan_tmp[32];
     K sk[kSortTile];
     uint32_t si[kSortTile];
+    uint32_t sd[kSortTile];
 };
 
 template <typename K>
-__global__ void __launch_bounds__(kSortThreads) k_sort_pass(
-    const K *__restrict__ qin, const uint32_t *__restrict__ iin, K *__restrict__ qout,
-    uint32_t *__restrict__ iout, uint64_t nq, SortNorm sn, int pass, SortMeta meta, uint32_t ntiles)
+__global__ void __launch_bounds__(kSortThreads) k_msd_scatter(const K *__restrict__ q, uint64_t nq, SortNorm sn,
+                                                              const uint32_t *__restrict__ offsets, uint32_t ntiles,
+                                                              K *__restrict__ out_q, uint32_t *__restrict__ out_i)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    SortPassSmem<K> &S = *reinterpret_cast<SortPassSmem<K> *>(smem_raw);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-
-    for (int i = tid; i < kSortWarps * 256; i += blockDim.x) (&S.wh[0][0])[i] = 0;
-    if (tid == 0) S.tile = atomicAdd(meta.tile_ctr + pass, 1u);
+    MsdSmem<K> &S = *reinterpret_cast<MsdSmem<K> *>(smem_raw);
+    const int nb = 1 << sn.dbits;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < nb; i += blockDim.x) S.cnt[i] = 0;
     __syncthreads();
-    const uint32_t tile = S.tile;
-    const uint64_t tile_base = static_cast<uint64_t>(tile) * kSortTile;
-    const uint32_t tile_n = static_cast<uint32_t>(nq - tile_base < kSortTile ? nq - tile_base : kSortTile);
-
-    // 1. load this warp's 256 elements and rank them stably within the warp
-    constexpr int R = kSortPerWarp / 32;
+    constexpr int R = kSortTile / kSortThreads;
+    const uint64_t base = static_cast<uint64_t>(blockIdx.x) * kSortTile;
+    const uint32_t tile_n = static_cast<uint32_t>(nq - base < kSortTile ? nq - base : kSortTile);
     K key[R];
-    uint32_t idx[R], dig[R], rank[R];
-    const uint64_t wbase = tile_base + warp * kSortPerWarp;
+    uint32_t dig[R], rank[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const uint64_t pos = wbase + r * 32 + lane;
-        if (pos < nq) {
-            key[r] = qin[pos];
-            idx[r] = iin ? iin[pos] : static_cast<uint32_t>(pos);
-        }
+        const uint64_t pos = base + r * kSortThreads + tid;
+        if (pos < nq) key[r] = q[pos];
     }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const uint64_t pos = wbase + r * 32 + lane;
+        const uint64_t pos = base + r * kSortThreads + tid;
         const bool valid = pos < nq;
         const unsigned vm = __ballot_sync(0xffffffffu, valid);
-        dig[r] = valid ? sort_digit(key[r], sn, pass) : 0u;
-        const unsigned same = warp_match8(dig[r], vm);
-        if (valid) rank[r] = S.wh[warp][dig[r]] + __popc(same & sort_lanemask_lt());
-        __syncwarp();
-        if (valid && (same & sort_lanemask_lt()) == 0) S.wh[warp][dig[r]] += __popc(same);
-        __syncwarp();
+        dig[r] = valid ? static_cast<uint32_t>(sort_field(key[r], sn, sn.dbits)) : 0u;
+        const unsigned same = warp_match_bits(dig[r], vm, sn.dbits);
+        const int leader = __ffs(same) - 1;
+        uint32_t b0 = 0;
+        if (valid && (tid & 31) == leader) b0 = atomicAdd(&S.cnt[dig[r]], __popc(same));
+        b0 = __shfl_sync(0xffffffffu, b0, leader < 0 ? 0 : leader);
+        if (valid) rank[r] = b0 + __popc(same & sort_lanemask_lt());
     }
     __syncthreads();
-
-    // 2. per digit: prefix over warps, tile count, publication, offsets
-    uint32_t tcnt = 0;
-    if (tid < 256) {
-        for (int w = 0; w < kSortWarps; ++w) {
-            const uint32_t v = S.wh[w][tid];
-            S.wh[w][tid] = tcnt;
-            tcnt += v;
+    // the tile's range in each bucket (scanned offsets), then local bucket starts
+    for (int i = tid; i < nb; i += blockDim.x) S.base[i] = offsets[static_cast<uint64_t>(i) * ntiles + blockIdx.x];
+    const int per = (nb + blockDim.x - 1) / blockDim.x;  // at most 8 buckets per thread
+    uint32_t c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    uint32_t sum = 0;
+    for (int k = 0; k < per; ++k) {
+        const int b = tid * per + k;
+        if (b < nb) {
+            c[k] = S.cnt[b];
+            sum += c[k];
         }
-        unsigned long long *st = meta.status + (static_cast<uint64_t>(pass) * ntiles + tile) * 256u + tid;
-        st_relaxed_u64(st, (tile == 0 ? kFlagIncl : kFlagAgg) | tcnt);
-    }
-    const uint32_t gh = (tid < 256) ? meta.ghist[pass * 256 + tid] : 0u;
-    const uint32_t gb = block_excl_scan256(gh, S.scan_tmp);
-    const uint32_t ts = block_excl_scan256(tcnt, S.scan_tmp);
-    if (tid < 256) {
-        S.gbase[tid] = gb;
-        S.tstart[tid] = ts;
     }
     __syncthreads();
-
-    // 3. reorder the tile by digit in shared memory (before the look-back,
-    //    so the elements' registers are free while it runs)
+    uint32_t run = block_excl_scan(sum, S.scan_tmp);
+    for (int k = 0; k < per; ++k) {
+        const int b = tid * per + k;
+        if (b < nb) S.cnt[b] = run;
+        run += c[k];
+    }
+    __syncthreads();
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const uint64_t pos = wbase + r * 32 + lane;
+        const uint64_t pos = base + r * kSortThreads + tid;
         if (pos < nq) {
-            const uint32_t lp = S.tstart[dig[r]] + S.wh[warp][dig[r]] + rank[r];
+            const uint32_t lp = S.cnt[dig[r]] + rank[r];
             S.sk[lp] = key[r];
-            S.si[lp] = idx[r];
+            S.si[lp] = static_cast<uint32_t>(pos);
+            S.sd[lp] = dig[r];
         }
-    }
-
-    if (tid < 256) {
-        // Decoupled look-back over the preceding tiles for this digit, a
-        // window of kLookbackWindow tiles per round trip: walking down from
-        // the nearest tile, add counts until a tile that already published
-        // its inclusive prefix; a tile that has published nothing yet makes
-        // the window be read again (bounded).
-        uint32_t excl = 0;
-        if (tile > 0) {
-            const unsigned long long *col = meta.status + static_cast<uint64_t>(pass) * ntiles * 256u + tid;
-            int64_t end = tile;
-            uint32_t spins = 0;
-            while (end > 0) {
-                const int64_t lo = end > kLookbackWindow ? end - kLookbackWindow : 0;
-                const int n = static_cast<int>(end - lo);
-                unsigned long long v[kLookbackWindow];
-#pragma unroll
-                for (int k = 0; k < kLookbackWindow; ++k)
-                    v[k] = (k < n) ? ld_relaxed_u64(col + static_cast<uint64_t>(lo + k) * 256u) : 0ull;
-                uint32_t acc = 0;
-                bool done = false, retry = false;
-#pragma unroll
-                for (int k = kLookbackWindow - 1; k >= 0; --k) {
-                    if (k < n && !done && !retry) {
-                        const unsigned long long flag = v[k] & (3ull << 62);
-                        if (flag == 0) {
-                            retry = true;
-                        } else {
-                            acc += static_cast<uint32_t>(v[k]);
-                            done = (flag == kFlagIncl);
-                        }
-                    }
-                }
-                if (retry) {
-                    if (++spins > kLookbackSpinLimit) {
-                        atomicOr(meta.err, 1u);
-                        break;
-                    }
-                    __nanosleep(64);
-                    continue;
-                }
-                excl += acc;
-                if (done) break;
-                end = lo;
-            }
-            unsigned long long *st = meta.status + (static_cast<uint64_t>(pass) * ntiles + tile) * 256u + tid;
-            st_relaxed_u64(st, kFlagIncl | (excl + tcnt));
-        }
-        S.tpref[tid] = excl;
     }
     __syncthreads();
-
-    // 4. write runs of equal digits to consecutive output positions
     for (uint32_t i = tid; i < tile_n; i += blockDim.x) {
-        const K k = S.sk[i];
-        const uint32_t d = sort_digit(k, sn, pass);
-        const uint32_t g = S.gbase[d] + S.tpref[d] + (i - S.tstart[d]);
-        qout[g] = k;
-        iout[g] = S.si[i];
+        const uint32_t d = S.sd[i];
+        const uint32_t g = S.base[d] + (i - S.cnt[d]);
+        out_q[g] = S.sk[i];
+        out_i[g] = S.si[i];
+    }
+}
+
+// ---------------------------------------------------------- 2. local sort
+
+template <typename K>
+struct LocalSmem {
+    uint32_t wh[kSortWarps][256];
+    uint32_t tstart[256];
+    uint32_t scan_tmp[32];
+    K sk[2][kSortTile];
+    uint32_t si[2][kSortTile];
+};
+
+// Sort every aligned run of kSortTile positions by the leading sn.bits bits,
+// in place (src == dst allowed) or from src to dst.  iin == nullptr: the
+// positions are the identity.
+template <typename K>
+__global__ void __launch_bounds__(kSortThreads) k_local_sort(const K *src_q, const uint32_t *src_i, K *dst_q,
+                                                             uint32_t *dst_i, uint64_t nq, SortNorm sn)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    LocalSmem<K> &S = *reinterpret_cast<LocalSmem<K> *>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint64_t base = static_cast<uint64_t>(blockIdx.x) * kSortTile;
+    const uint32_t n = static_cast<uint32_t>(nq - base < kSortTile ? nq - base : kSortTile);
+    {
+        constexpr int RL = kSortTile / kSortThreads;  // all loads in flight before the stores
+        K kk[RL];
+        uint32_t ii[RL];
+#pragma unroll
+        for (int r = 0; r < RL; ++r) {
+            const uint32_t i = r * kSortThreads + tid;
+            if (i < n) {
+                kk[r] = src_q[base + i];
+                ii[r] = src_i ? src_i[base + i] : static_cast<uint32_t>(base + i);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < RL; ++r) {
+            const uint32_t i = r * kSortThreads + tid;
+            if (i < n) {
+                S.sk[0][i] = kk[r];
+                S.si[0][i] = ii[r];
+            }
+        }
+    }
+    __syncthreads();
+    const int passes = (sn.bits + 7) / 8;
+    int cur = 0;
+    constexpr int R = kSortPerWarp / 32;
+    for (int p = 0; p < passes; ++p) {
+        const int lo = 8 * p;  // bit offset of this digit within the field
+        const int w = sn.bits - lo < 8 ? sn.bits - lo : 8;
+        for (int i = tid; i < kSortWarps * 256; i += blockDim.x) (&S.wh[0][0])[i] = 0;
+        __syncthreads();
+        uint32_t dig[R], rank[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const uint32_t i = warp * kSortPerWarp + r * 32 + lane;
+            const bool valid = i < n;
+            const unsigned vm = __ballot_sync(0xffffffffu, valid);
+            dig[r] = valid ? static_cast<uint32_t>((sort_field(S.sk[cur][i], sn, sn.bits) >> lo) & ((1u << w) - 1u)) : 0u;
+            const unsigned same = warp_match_bits(dig[r], vm, w);
+            if (valid) rank[r] = S.wh[warp][dig[r]] + __popc(same & sort_lanemask_lt());
+            __syncwarp();
+            if (valid && (same & sort_lanemask_lt()) == 0) S.wh[warp][dig[r]] += __popc(same);
+            __syncwarp();
+        }
+        __syncthreads();
+        uint32_t tcnt = 0;
+        if (tid < 256) {
+            for (int ww = 0; ww < kSortWarps; ++ww) {
+                const uint32_t v = S.wh[ww][tid];
+                S.wh[ww][tid] = tcnt;
+                tcnt += v;
+            }
+        }
+        const uint32_t ts = block_excl_scan(tcnt, S.scan_tmp);
+        if (tid < 256) S.tstart[tid] = ts;
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const uint32_t i = warp * kSortPerWarp + r * 32 + lane;
+            if (i < n) {
+                const uint32_t lp = S.tstart[dig[r]] + S.wh[warp][dig[r]] + rank[r];
+                S.sk[cur ^ 1][lp] = S.sk[cur][i];
+                S.si[cur ^ 1][lp] = S.si[cur][i];
+            }
+        }
+        __syncthreads();
+        cur ^= 1;
+    }
+    for (uint32_t i = tid; i < n; i += blockDim.x) {
+        dst_q[base + i] = S.sk[cur][i];
+        dst_i[base + i] = S.si[cur][i];
     }
 }
 
 template <typename K>
-constexpr int sort_pass_smem_bytes()
+constexpr int msd_smem_bytes()
 {
-    return static_cast<int>(sizeof(SortPassSmem<K>));
+    return static_cast<int>(sizeof(MsdSmem<K>));
+}
+
+template <typename K>
+constexpr int local_smem_bytes()
+{
+    return static_cast<int>(sizeof(LocalSmem<K>));
 }
 
 }  // namespace btgb

@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstring>
 
 #include "bt_internal.h"
 #include "radix_sort.cuh"
@@ -56,8 +57,8 @@ __device__ __forceinline__ unsigned lanemask_lt()
 
 // -------------------------------------------- level-wise descent (a3-a5)
 //
-// Persistent blocks of kDescWarps warps.  Each block first copies the top
-// levels of the tree (as many whole levels as fit kPinBudget bytes, never
+// Persistent blocks of a tunable number of warps.  Each block first copies the top
+// levels of the tree (as many whole levels as fit the tree's pin budget, never
 // the leaves) into shared memory once; a warp then loops over chunks of 32
 // consecutive queries of the (sorted) batch, prefetching the next chunk's
 // queries and output positions while it works on the current one.  Per
@@ -65,8 +66,9 @@ __device__ __forceinline__ unsigned lanemask_lt()
 // its shared-memory slots (rounds of `stage_slots` nodes) before the binary
 // searches.
 
-constexpr int kDescWarps = 8;
-constexpr int kPinBudget = 16384;
+constexpr int kDescWarpsDefault = 8;
+constexpr int kDescWarpsMax = 16;
+constexpr int kPinBudgetMax = 49152;
 
 template <typename K, int M>
 constexpr int stage_slots()
@@ -75,9 +77,9 @@ constexpr int stage_slots()
 }
 
 template <typename K, int M>
-constexpr int desc_smem_fixed()
+constexpr int desc_smem_per_warp()
 {
-    return kDescWarps * (stage_slots<K, M>() * M * static_cast<int>(sizeof(K)) + 32 * 4);
+    return stage_slots<K, M>() * M * static_cast<int>(sizeof(K)) + 32 * 4;
 }
 
 // Number of slots of a node block holding a key smaller than `key`: the
@@ -120,36 +122,80 @@ __device__ __forceinline__ void warp_distinct(uint32_t node, int lane, uint32_t 
     }
 }
 
+// First child of inner node `node` of level l plus rank r.  32-bit: an
+// inner node has at most 64 children and every level has < 2^32 nodes.
 __device__ __forceinline__ uint32_t child_of(const DevTree &t, int l, uint32_t node, int r)
 {
-    const uint64_t base = t.cbase[l], rem = t.crem[l];
-    return static_cast<uint32_t>(node * base + (node < rem ? node : rem) + r);
+    const uint32_t base = static_cast<uint32_t>(t.cbase[l]), rem = static_cast<uint32_t>(t.crem[l]);
+    return node * base + (node < rem ? node : rem) + static_cast<uint32_t>(r);
 }
 
-template <typename K, typename V, int M, bool COUNT>
-__global__ void __launch_bounds__(kDescWarps * 32) k_descend(
+// Leaf-max entries a warp can stage for its model windows.
+constexpr int kLeafMaxCap = 128;
+// PL models with at most this many segments are copied to shared memory.
+constexpr uint32_t kModelSmemSegments = 512;
+
+__host__ __device__ inline uint32_t model_smem_bytes(const ModelDev &m)
+{
+    if (m.kind == kModelPL) return m.segments <= kModelSmemSegments ? (m.segments * 20u + 15u) / 16u * 16u : 0u;
+    if (m.kind == kModelMLP) return (kMlpParams * 4u + 15u) / 16u * 16u;
+    return 0u;
+}
+
+template <typename K, typename V, int M, bool COUNT, bool LEARN>
+__global__ void __launch_bounds__(kDescWarpsMax * 32) k_descend(
     const DevTree t, const K *__restrict__ q, const uint32_t *__restrict__ qidx, uint64_t nq,
-    V *__restrict__ out_v, uint8_t *__restrict__ out_f, unsigned long long *__restrict__ fetch)
+    V *__restrict__ out_v, uint8_t *__restrict__ out_f, unsigned long long *__restrict__ fetch,
+    const ModelDev md, unsigned long long *__restrict__ lstats)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int CH = M * static_cast<int>(sizeof(K)) / 16;  // 16-byte chunks per node block
     constexpr int SLOTS = stage_slots<K, M>();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t pin_bytes = t.pin_bytes;
+    const uint32_t mbytes = LEARN ? model_smem_bytes(md) : 0u;
     unsigned char *pin = smem;
-    K *stage = reinterpret_cast<K *>(smem + pin_bytes) + warp * SLOTS * M;
-    uint32_t *list = reinterpret_cast<uint32_t *>(smem + pin_bytes + kDescWarps * SLOTS * M * sizeof(K)) + warp * 32;
+    unsigned char *msm = smem + pin_bytes;
+    K *stage = reinterpret_cast<K *>(msm + mbytes) + warp * SLOTS * M;
+    const int nw = blockDim.x >> 5;
+    unsigned char *after_stage = msm + mbytes + nw * SLOTS * M * sizeof(K);
+    uint32_t *list = reinterpret_cast<uint32_t *>(after_stage) + warp * 32;
+    K *lmstage = reinterpret_cast<K *>(after_stage + nw * 32 * 4) + warp * kLeafMaxCap;
 
     // Top levels, pinned once per block.
     const unsigned char *top = static_cast<const unsigned char *>(t.keys[0]);
     for (uint32_t i = threadIdx.x * 16u; i < pin_bytes; i += blockDim.x * 16u) cp_async16_ca(pin + i, top + i);
+    // The model's parameters, copied once per block when they fit.
+    const uint64_t *mb = md.b;
+    const float *minv = md.inv_w, *mslope = md.slope, *micpt = md.icpt, *mmlp = md.mlp;
+    if (LEARN && mbytes) {
+        if (md.kind == kModelPL) {
+            const uint32_t S = md.segments;
+            uint64_t *sb = reinterpret_cast<uint64_t *>(msm);
+            float *sf = reinterpret_cast<float *>(msm + S * 8u);
+            for (uint32_t i = threadIdx.x; i < S; i += blockDim.x) {
+                sb[i] = md.b[i];
+                sf[i] = md.inv_w[i];
+                sf[S + i] = md.slope[i];
+                sf[2 * S + i] = md.icpt[i];
+            }
+            mb = sb;
+            minv = sf;
+            mslope = sf + S;
+            micpt = sf + 2 * S;
+        } else {
+            float *sp = reinterpret_cast<float *>(msm);
+            for (uint32_t i = threadIdx.x; i < static_cast<uint32_t>(kMlpParams); i += blockDim.x) sp[i] = md.mlp[i];
+            mmlp = sp;
+        }
+    }
     cp_async_wait_all();
     __syncthreads();
 
     const uint64_t nchunks = (nq + 31) / 32;
-    const uint64_t stride = static_cast<uint64_t>(gridDim.x) * kDescWarps;
+    const uint64_t stride = static_cast<uint64_t>(gridDim.x) * nw;
     const int H = t.height, P = t.pin_levels;
-    uint64_t c = static_cast<uint64_t>(blockIdx.x) * kDescWarps + warp;
+    uint64_t c = static_cast<uint64_t>(blockIdx.x) * nw + warp;
     if (c >= nchunks) return;
 
     // Tail lanes follow lane 0's query so they never add a node fetch.
@@ -161,6 +207,12 @@ __global__ void __launch_bounds__(kDescWarps * 32) k_descend(
         key_n = q[v ? pos : c * 32];
         dst_n = v ? (qidx ? qidx[pos] : static_cast<uint32_t>(pos)) : 0u;
     }
+    // The previous chunk's result: its value load is issued at its leaf
+    // level and consumed (stored) only after this chunk's first staged level,
+    // so the load's latency overlaps the next descent.
+    V pend_val = 0;
+    uint32_t pend_dst = 0;
+    bool pend_store = false, pend_hit = false;
     for (;;) {
         const uint64_t pos = c * 32 + lane;
         const bool valid = pos < nq;
@@ -176,6 +228,50 @@ __global__ void __launch_bounds__(kDescWarps * 32) k_descend(
 
         uint32_t node = 0;
         int l = 0;
+        if (LEARN) {
+            // Predicted leaf and its error window; the warp stages the leaf
+            // maxima covering all its windows (plus the leaf below) and every
+            // lane proves its leaf: the first window leaf whose largest key
+            // is >= the query, with the leaf below the window ending below
+            // the query.  One unproven lane sends the warp down the tree.
+            const uint32_t L = md.leaves;
+            const uint32_t hat = model_leaf(md, mb, minv, mslope, micpt, mmlp, static_cast<uint64_t>(key));
+            const uint32_t lo = hat > md.err ? hat - md.err : 0u;
+            const uint32_t hi = (static_cast<uint64_t>(hat) + md.err < L) ? hat + md.err : L - 1;
+            uint32_t wlo = __reduce_min_sync(0xffffffffu, lo);
+            if (wlo > 0) --wlo;
+            const uint32_t whi = __reduce_max_sync(0xffffffffu, hi);
+            bool ok = false;
+            uint32_t leaf = 0;
+            if (whi - wlo < static_cast<uint32_t>(kLeafMaxCap)) {
+                const K *lm = static_cast<const K *>(md.leaf_max);
+                for (uint32_t j = lane; j <= whi - wlo; j += 32) lmstage[j] = lm[wlo + j];
+                __syncwarp();
+                const bool low_ok = (lo == 0) || (key > lmstage[lo - 1 - wlo]);
+                uint32_t a = lo, e = hi + 1;  // first j in [lo, hi] with key <= leaf_max[j]
+                while (a < e) {
+                    const uint32_t mid = (a + e) >> 1;
+                    if (lmstage[mid - wlo] < key)
+                        a = mid + 1;
+                    else
+                        e = mid;
+                }
+                if (a <= hi) {
+                    leaf = a;
+                    ok = low_ok;
+                } else if (hi == L - 1) {  // above every key: the last leaf
+                    leaf = L - 1;
+                    ok = low_ok;
+                }
+                __syncwarp();
+            }
+            const bool all_ok = __all_sync(0xffffffffu, ok);
+            if (lstats && lane == 0) atomicAdd(lstats + (all_ok ? 0 : 1), 1ull);
+            if (all_ok) {
+                node = leaf;
+                l = H - 1;
+            }
+        }
         for (; l < P; ++l) {  // pinned levels: search the block's shared copy
             if (COUNT) {
                 int U, slot;
@@ -219,21 +315,29 @@ __global__ void __launch_bounds__(kDescWarps * 32) k_descend(
                 }
                 __syncwarp();
             }
+            if (pend_store) {  // previous chunk's result, after this chunk's first staged level
+                out_v[pend_dst] = pend_val;
+                out_f[pend_dst] = pend_hit ? 1 : 0;
+                pend_store = false;
+            }
             if (!last) {
                 node = child_of(t, l, node, r);
             } else {
                 const uint64_t cnt = t.cbase[l] + (node < t.crem[l] ? 1u : 0u);
                 const bool hit = (static_cast<uint64_t>(r) < cnt) && eq;
-                V val = static_cast<V>(~static_cast<V>(0));
-                if (hit) val = static_cast<const V *>(t.vals)[static_cast<uint64_t>(node) * M + r];
-                if (valid) {
-                    out_v[dst] = val;
-                    out_f[dst] = hit ? 1 : 0;
-                }
+                pend_val = static_cast<V>(~static_cast<V>(0));
+                if (hit) pend_val = static_cast<const V *>(t.vals)[static_cast<uint64_t>(node) * M + r];
+                pend_hit = hit;
+                pend_dst = dst;
+                pend_store = valid;
             }
         }
         if (cn >= nchunks) break;
         c = cn;
+    }
+    if (pend_store) {
+        out_v[pend_dst] = pend_val;
+        out_f[pend_dst] = pend_hit ? 1 : 0;
     }
 }
 
@@ -254,12 +358,23 @@ static inline uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
 static inline uint32_t sort_tiles(uint64_t nq) { return static_cast<uint32_t>((nq + kSortTile - 1) / kSortTile); }
 
 struct WsLayout {
-    uint64_t qa, ia, qb, ib, meta, status, total;
+    uint64_t qa, ia, qb, ib, counts, total;
 };
 
-// Workspace: two ping-pong (query, position) buffers, then the sort's
-// metadata block (global digit histograms, tile counters, error word) and
-// the per-tile look-back status words.
+// Largest distribution width for a batch: about nq / tile buckets, at most
+// 2^12 buckets and at most kMaxBucketTiles (bucket, tile) pairs.
+static int dist_bits_max(uint64_t nq)
+{
+    const uint64_t ntiles = (nq + kSortTile - 1) / kSortTile;
+    int db = 0;
+    while (db < kMaxDistBits && (static_cast<uint64_t>(kSortTile) << db) < nq &&
+           (ntiles << (db + 1)) <= kMaxBucketTiles)
+        ++db;
+    return db;
+}
+
+// Workspace: two (query, position) buffers -- the distribution's output and
+// the sorted batch -- then the distribution's [bucket][tile] count matrix.
 static WsLayout ws_layout(int kb, uint64_t nq)
 {
     WsLayout w;
@@ -272,94 +387,111 @@ static WsLayout ws_layout(int kb, uint64_t nq)
     o = align256(o + nq * kb);
     w.ib = o;
     o = align256(o + nq * 4);
-    w.meta = o;
-    o = align256(o + (kMaxPasses * 256 + kMaxPasses + 1) * 4);
-    w.status = o;
-    o = align256(o + static_cast<uint64_t>(kMaxPasses) * sort_tiles(nq) * 256u * 8u);
+    w.counts = o;
+    o = align256(o + (static_cast<uint64_t>(sort_tiles(nq)) << dist_bits_max(nq)) * 4);
     w.total = nq ? o : 0;
     return w;
-}
-
-static SortMeta sort_meta(unsigned char *ws, const WsLayout &w)
-{
-    SortMeta m;
-    m.ghist = reinterpret_cast<uint32_t *>(ws + w.meta);
-    m.tile_ctr = m.ghist + kMaxPasses * 256;
-    m.err = m.tile_ctr + kMaxPasses;
-    m.status = reinterpret_cast<unsigned long long *>(ws + w.status);
-    return m;
 }
 
 static int bitlen(uint64_t x) { return x ? 64 - __builtin_clzll(x) : 0; }
 
 // Queries per batch from which the sort pays for itself by node reuse.
 constexpr uint64_t kAutoSortMinBatch = 16384;
-constexpr int kAutoSortBits = 16;
+// Bits ordered within a tile below the distribution's bucket bits.
+constexpr int kAutoLocalBits = 8;
 
-template <typename K, typename V, int M, bool COUNT>
-static cudaError_t launch_descend(const DevTree &t, const void *q, const uint32_t *qidx, uint64_t nq,
-                                  void *out_v, uint8_t *out_f, unsigned long long *fetch,
-                                  cudaStream_t s)
+// One search's descent launch: everything a kernel instantiation needs.
+struct DescendArgs {
+    const DevTree *t;
+    const void *q;
+    const uint32_t *qidx;
+    uint64_t nq;
+    void *out_v;
+    uint8_t *out_f;
+    unsigned long long *fetch;
+    const ModelDev *md;  // non-null: learned descent
+    unsigned long long *lstats;
+};
+
+template <typename K, typename V, int M, bool COUNT, bool LEARN>
+static cudaError_t launch_descend(const DescendArgs &a, cudaStream_t s)
 {
-    constexpr int fixed = desc_smem_fixed<K, M>();
-    constexpr int threads = kDescWarps * 32;
-    auto kern = k_descend<K, V, M, COUNT>;
-    static const cudaError_t attr =
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, fixed + kPinBudget);
+    const int nw = a.t->warps > 0 ? a.t->warps : kDescWarpsDefault;
+    const int fixed = nw * desc_smem_per_warp<K, M>();
+    const int learn_fixed = LEARN ? nw * kLeafMaxCap * static_cast<int>(sizeof(K)) : 0;
+    constexpr int max_model = LEARN ? static_cast<int>(kModelSmemSegments) * 20 : 0;
+    const int threads = nw * 32;
+    auto kern = k_descend<K, V, M, COUNT, LEARN>;
+    static const cudaError_t attr = cudaFuncSetAttribute(
+        kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        kDescWarpsMax * (desc_smem_per_warp<K, M>() + (LEARN ? kLeafMaxCap * static_cast<int>(sizeof(K)) : 0)) +
+            kPinBudgetMax + max_model);
     if (attr != cudaSuccess) return attr;
-    const int smem = fixed + static_cast<int>(t.pin_bytes);
-    // resident blocks per SM for this shared-memory size (cached per size)
-    static int occ_cache[kPinBudget / 256 + 2] = {0};
-    const int key = static_cast<int>((t.pin_bytes + 255) / 256);
-    if (occ_cache[key] == 0) {
+    ModelDev none;
+    memset(&none, 0, sizeof(none));
+    const ModelDev &md = a.md ? *a.md : none;
+    const int smem = fixed + learn_fixed + static_cast<int>(a.t->pin_bytes) +
+                     static_cast<int>(LEARN ? model_smem_bytes(md) : 0u);
+    // resident blocks per SM for this block size and shared-memory size
+    // (cached per warp count and 256 bytes of shared memory)
+    constexpr int kCache = (kPinBudgetMax + max_model) / 256 + 2;
+    static int occ_cache[kDescWarpsMax + 1][kCache] = {{0}};
+    const int key = (smem - fixed - learn_fixed + 255) / 256;
+    if (occ_cache[nw][key] == 0) {
         int b = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, threads, fixed + key * 256);
+        cudaError_t e =
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, threads, fixed + learn_fixed + key * 256);
         if (e != cudaSuccess) return e;
-        occ_cache[key] = b > 0 ? b : 1;
+        occ_cache[nw][key] = b > 0 ? b : 1;
     }
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    const uint64_t chunks = (nq + 31) / 32;
-    uint64_t grid = (chunks + kDescWarps - 1) / kDescWarps;
-    const uint64_t cap = static_cast<uint64_t>(sms) * occ_cache[key];
+    const uint64_t chunks = (a.nq + 31) / 32;
+    uint64_t grid = (chunks + nw - 1) / nw;
+    const uint64_t cap = static_cast<uint64_t>(sms) * occ_cache[nw][key];
     if (grid > cap) grid = cap;
-    kern<<<static_cast<unsigned>(grid), threads, smem, s>>>(t, static_cast<const K *>(q), qidx, nq,
-                                                           static_cast<V *>(out_v), out_f, fetch);
+    kern<<<static_cast<unsigned>(grid), threads, smem, s>>>(*a.t, static_cast<const K *>(a.q), a.qidx, a.nq,
+                                                           static_cast<V *>(a.out_v), a.out_f, a.fetch, md,
+                                                           a.lstats);
     return cudaGetLastError();
 }
 
 template <typename K, typename V, int M>
-static cudaError_t dispatch_count(const DevTree &t, const void *q, const uint32_t *qidx, uint64_t nq,
-                                  void *out_v, uint8_t *out_f, unsigned long long *fetch,
-                                  cudaStream_t s)
+static cudaError_t dispatch_mode(const DescendArgs &a, cudaStream_t s)
 {
-    if (fetch) return launch_descend<K, V, M, true>(t, q, qidx, nq, out_v, out_f, fetch, s);
-    return launch_descend<K, V, M, false>(t, q, qidx, nq, out_v, out_f, nullptr, s);
+    if (a.md) return launch_descend<K, V, M, false, true>(a, s);
+    if (a.fetch) return launch_descend<K, V, M, true, false>(a, s);
+    return launch_descend<K, V, M, false, false>(a, s);
 }
 
 template <typename K, typename V>
-static cudaError_t dispatch_m(const DevTree &t, const void *q, const uint32_t *qidx, uint64_t nq,
-                              void *out_v, uint8_t *out_f, unsigned long long *fetch, cudaStream_t s)
+static cudaError_t dispatch_m(const DescendArgs &a, cudaStream_t s)
 {
-    switch (t.m) {
-    case 8: return dispatch_count<K, V, 8>(t, q, qidx, nq, out_v, out_f, fetch, s);
-    case 16: return dispatch_count<K, V, 16>(t, q, qidx, nq, out_v, out_f, fetch, s);
-    case 32: return dispatch_count<K, V, 32>(t, q, qidx, nq, out_v, out_f, fetch, s);
-    default: return dispatch_count<K, V, 64>(t, q, qidx, nq, out_v, out_f, fetch, s);
+    switch (a.t->m) {
+    case 8: return dispatch_mode<K, V, 8>(a, s);
+    case 16: return dispatch_mode<K, V, 16>(a, s);
+    case 32: return dispatch_mode<K, V, 32>(a, s);
+    default: return dispatch_mode<K, V, 64>(a, s);
     }
+}
+
+static cudaError_t descend_any(const DescendArgs &a, cudaStream_t s)
+{
+    if (a.t->key_bytes == 8) {
+        if (a.t->val_bytes == 8) return dispatch_m<uint64_t, uint64_t>(a, s);
+        return dispatch_m<uint64_t, uint32_t>(a, s);
+    }
+    if (a.t->val_bytes == 8) return dispatch_m<uint32_t, uint64_t>(a, s);
+    return dispatch_m<uint32_t, uint32_t>(a, s);
 }
 
 static cudaError_t descend(const DevTree &t, const void *q, const uint32_t *qidx, uint64_t nq,
                            void *out_v, uint8_t *out_f, unsigned long long *fetch, cudaStream_t s)
 {
-    if (t.key_bytes == 8) {
-        if (t.val_bytes == 8) return dispatch_m<uint64_t, uint64_t>(t, q, qidx, nq, out_v, out_f, fetch, s);
-        return dispatch_m<uint64_t, uint32_t>(t, q, qidx, nq, out_v, out_f, fetch, s);
-    }
-    if (t.val_bytes == 8) return dispatch_m<uint32_t, uint64_t>(t, q, qidx, nq, out_v, out_f, fetch, s);
-    return dispatch_m<uint32_t, uint32_t>(t, q, qidx, nq, out_v, out_f, fetch, s);
+    const DescendArgs a{&t, q, qidx, nq, out_v, out_f, fetch, nullptr, nullptr};
+    return descend_any(a, s);
 }
 
 template <typename K>
@@ -373,46 +505,45 @@ __global__ void k_copy_identity(const K *__restrict__ q, K *__restrict__ qo, uin
     }
 }
 
-// Sort (query, position) pairs: passes before the last ping-pong between the
-// workspace buffers A and B (A first), the last pass writes (dst_q, dst_i).
+// The two-stage sort of (query, position) pairs into (dst_q, dst_i): the
+// distribution into workspace buffer A (skipped when dbits == 0), then the
+// per-tile local sort from A (or from the queries) into the destination.
 template <typename K>
 static cudaError_t radix_sort(const K *q, uint64_t nq, const SortNorm &sn, unsigned char *ws,
                               const WsLayout &w, K *dst_q, uint32_t *dst_i, cudaStream_t s)
 {
     const uint32_t ntiles = sort_tiles(nq);
-    const SortMeta meta = sort_meta(ws, w);
-    // histograms, tile counters, error word and the used status words start at zero
-    cudaError_t e = cudaMemsetAsync(ws + w.meta, 0,
-                                    (w.status - w.meta) + static_cast<uint64_t>(sn.passes) * ntiles * 256u * 8u, s);
-    if (e != cudaSuccess) return e;
-    constexpr int smem = sort_pass_smem_bytes<K>();
-    static const cudaError_t attr =
-        cudaFuncSetAttribute(k_sort_pass<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (attr != cudaSuccess) return attr;
-    k_sort_hist<K><<<ntiles, kSortThreads, 0, s>>>(q, nq, sn, meta.ghist);
-    K *qa = reinterpret_cast<K *>(ws + w.qa), *qb = reinterpret_cast<K *>(ws + w.qb);
-    uint32_t *ia = reinterpret_cast<uint32_t *>(ws + w.ia), *ib = reinterpret_cast<uint32_t *>(ws + w.ib);
+    cudaError_t e;
     const K *src_q = q;
     const uint32_t *src_i = nullptr;
-    for (int p = 0; p < sn.passes; ++p) {
-        const bool final_pass = (p + 1 == sn.passes);
-        K *dq = final_pass ? dst_q : ((p & 1) ? qb : qa);
-        uint32_t *di = final_pass ? dst_i : ((p & 1) ? ib : ia);
-        k_sort_pass<K><<<ntiles, kSortThreads, smem, s>>>(src_q, src_i, dq, di, nq, sn, p, meta, ntiles);
-        src_q = dq;
-        src_i = di;
+    if (sn.dbits > 0) {
+        const uint32_t nb = 1u << sn.dbits;
+        uint32_t *counts = reinterpret_cast<uint32_t *>(ws + w.counts);
+        constexpr int msmem = msd_smem_bytes<K>();
+        static const cudaError_t attr =
+            cudaFuncSetAttribute(k_msd_scatter<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, msmem);
+        if (attr != cudaSuccess) return attr;
+        K *qa = reinterpret_cast<K *>(ws + w.qa);
+        uint32_t *ia = reinterpret_cast<uint32_t *>(ws + w.ia);
+        k_msd_hist<K><<<ntiles, kSortThreads, 0, s>>>(q, nq, sn, counts, ntiles);
+        k_msd_offsets<<<1, 1024, 0, s>>>(counts, nb * ntiles);
+        k_msd_scatter<K><<<ntiles, kSortThreads, msmem, s>>>(q, nq, sn, counts, ntiles, qa, ia);
+        src_q = qa;
+        src_i = ia;
     }
+    constexpr int lsmem = local_smem_bytes<K>();
+    static const cudaError_t lattr =
+        cudaFuncSetAttribute(k_local_sort<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, lsmem);
+    if (lattr != cudaSuccess) return lattr;
+    k_local_sort<K><<<ntiles, kSortThreads, lsmem, s>>>(src_q, src_i, dst_q, dst_i, nq, sn);
     return cudaGetLastError();
 }
 
-// Where bt_search_batch puts the sorted batch: whichever of A/B the last
-// intermediate pass did not write.
-static void internal_sort_dst(const SortNorm &sn, unsigned char *ws, const WsLayout &w, void **dq,
-                              uint32_t **di)
+// Where bt_search_batch puts the sorted batch: workspace buffer B.
+static void internal_sort_dst(unsigned char *ws, const WsLayout &w, void **dq, uint32_t **di)
 {
-    const bool use_b = sn.passes >= 2 && ((sn.passes - 2) % 2 == 0);
-    *dq = ws + (use_b ? w.qb : w.qa);
-    *di = reinterpret_cast<uint32_t *>(ws + (use_b ? w.ib : w.ia));
+    *dq = ws + w.qb;
+    *di = reinterpret_cast<uint32_t *>(ws + w.ib);
 }
 
 static cudaError_t sort_any(const DevTree &t, const void *q, uint64_t nq, const SortNorm &sn,
@@ -426,18 +557,22 @@ static cudaError_t sort_any(const DevTree &t, const void *q, uint64_t nq, const 
                                 static_cast<uint32_t *>(dq), di, s);
 }
 
+// Sort parameters for this tree and batch.  sort_bits < 0: kAutoLocalBits
+// bits within tiles below the distribution's bucket bits, for batches of at
+// least kAutoSortMinBatch queries, else no sort.  sort_bits > 0: that many
+// leading bits within tiles (capped at the key range and width).
 static SortNorm make_norm(const DevTree &t, int32_t sort_bits, uint64_t nq)
 {
-    SortNorm sn{t.kmin, t.kmax - t.kmin, 0, 0};
+    SortNorm sn{t.kmin, t.kmax - t.kmin, 0, 0, 0};
+    sn.rl = bitlen(sn.range);
+    const int db = dist_bits_max(nq);
     int bits = sort_bits;
-    if (bits < 0) bits = (nq >= kAutoSortMinBatch) ? kAutoSortBits : 0;
-    const int rl = bitlen(sn.range);
-    if (bits > rl) bits = rl;
+    if (bits < 0) bits = (nq >= kAutoSortMinBatch) ? db + kAutoLocalBits : 0;
+    if (bits > sn.rl) bits = sn.rl;
     if (bits > 8 * t.key_bytes) bits = 8 * t.key_bytes;
     if (bits <= 0) return sn;
-    sn.passes = (bits + 7) / 8;
-    const int used = 8 * sn.passes;
-    sn.shift = rl > used ? rl - used : 0;
+    sn.bits = bits;
+    sn.dbits = db < bits ? db : bits;
     return sn;
 }
 
@@ -445,27 +580,13 @@ static SortNorm make_norm(const DevTree &t, int32_t sort_bits, uint64_t nq)
 
 using namespace btgb;
 
-extern "C" bt_status bt_workspace_status(const bt_tree *tree, const void *d_workspace, uint64_t nq)
-{
-    if (!tree || !d_workspace) return BT_ERR_ARG;
-    if (nq == 0) return BT_OK;
-    const WsLayout w = ws_layout(tree->dev.key_bytes, nq);
-    uint32_t err = 0;
-    const unsigned char *ws = static_cast<const unsigned char *>(d_workspace);
-    cudaError_t e = cudaMemcpy(&err, ws + w.meta + (kMaxPasses * 256 + kMaxPasses) * 4, 4,
-                               cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) {
-        set_error_detail("workspace status read", e);
-        return BT_ERR_CUDA;
-    }
-    return err ? BT_ERR_TIMEOUT : BT_OK;
-}
-
-extern "C" int32_t bt_sort_passes(const bt_tree *tree, uint64_t nq, int32_t sort_bits)
+extern "C" int32_t bt_sort_launches(const bt_tree *tree, uint64_t nq, int32_t sort_bits)
 {
     if (!tree) return -1;
     if (tree->dev.height == 0 || nq == 0) return 0;
-    return make_norm(tree->dev, sort_bits, nq).passes;
+    const SortNorm sn = make_norm(tree->dev, sort_bits, nq);
+    if (sn.bits == 0) return 0;
+    return sn.dbits > 0 ? 4 : 1;
 }
 
 extern "C" uint64_t bt_search_workspace_bytes(const bt_tree *tree, uint64_t nq)
@@ -515,10 +636,10 @@ extern "C" bt_status bt_search_batch_ex(const bt_tree *tree, const void *d_queri
     const void *q = d_queries;
     const uint32_t *qidx = nullptr;
     unsigned char *ws = static_cast<unsigned char *>(d_workspace);
-    if (sn.passes > 0) {
+    if (sn.bits > 0) {
         void *dq;
         uint32_t *di;
-        internal_sort_dst(sn, ws, w, &dq, &di);
+        internal_sort_dst(ws, w, &dq, &di);
         e = sort_any(t, d_queries, nq, sn, ws, w, dq, di, s);
         if (e != cudaSuccess) {
             set_error_detail("radix sort launch", e);
@@ -593,7 +714,7 @@ extern "C" bt_status bt_sort_batch(const bt_tree *tree, const void *d_queries, u
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const SortNorm sn = make_norm(t, sort_bits, nq);
     cudaError_t e;
-    if (sn.passes == 0) {
+    if (sn.bits == 0) {
         const unsigned grid = static_cast<unsigned>((nq + 255) / 256 < 4096 ? (nq + 255) / 256 : 4096);
         if (t.key_bytes == 8)
             k_copy_identity<uint64_t><<<grid, 256, 0, s>>>(static_cast<const uint64_t *>(d_queries),
@@ -638,6 +759,65 @@ extern "C" bt_status bt_descend_sorted(const bt_tree *tree, const void *d_querie
     }
     if (e != cudaSuccess) {
         set_error_detail("descent launch", e);
+        return BT_ERR_CUDA;
+    }
+    return BT_OK;
+}
+
+extern "C" bt_status bt_learned_descend_sorted(const bt_tree *tree, const bt_model *model, const void *d_queries,
+                                               const uint32_t *d_index, uint64_t nq, void *d_out_vals,
+                                               uint8_t *d_out_found, unsigned long long *d_stats, bt_stream stream)
+{
+    if (!tree || !model) return BT_ERR_ARG;
+    if (nq == 0) return BT_OK;
+    if (nq >= (1ull << 31)) return BT_ERR_ARG;
+    if (!d_queries || !d_out_vals || !d_out_found) return BT_ERR_ARG;
+    const DevTree &t = tree->dev;
+    if (t.height == 0 || model->dev.leaves != t.nodes[t.height - 1]) return BT_ERR_ARG;
+    const DescendArgs a{&t, d_queries, d_index, nq, d_out_vals, d_out_found, nullptr, &model->dev, d_stats};
+    const cudaError_t e = descend_any(a, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) {
+        set_error_detail("learned descent launch", e);
+        return BT_ERR_CUDA;
+    }
+    return BT_OK;
+}
+
+extern "C" bt_status bt_learned_search_batch(const bt_tree *tree, const bt_model *model, const void *d_queries,
+                                             uint64_t nq, void *d_out_vals, uint8_t *d_out_found, void *d_workspace,
+                                             uint64_t ws_bytes, bt_stream stream)
+{
+    if (!tree || !model) return BT_ERR_ARG;
+    if (nq == 0) return BT_OK;
+    if (nq >= (1ull << 31)) return BT_ERR_ARG;
+    if (!d_queries || !d_out_vals || !d_out_found) return BT_ERR_ARG;
+    const DevTree &t = tree->dev;
+    if (t.height == 0 || model->dev.leaves != t.nodes[t.height - 1]) return BT_ERR_ARG;
+    const WsLayout w = ws_layout(t.key_bytes, nq);
+    if (!d_workspace || ws_bytes < w.total || (reinterpret_cast<uintptr_t>(d_workspace) & 255u))
+        return BT_ERR_WORKSPACE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const SortNorm sn = make_norm(t, -1, nq);
+    const void *q = d_queries;
+    const uint32_t *qidx = nullptr;
+    unsigned char *ws = static_cast<unsigned char *>(d_workspace);
+    cudaError_t e;
+    if (sn.bits > 0) {
+        void *dq;
+        uint32_t *di;
+        internal_sort_dst(ws, w, &dq, &di);
+        e = sort_any(t, d_queries, nq, sn, ws, w, dq, di, s);
+        if (e != cudaSuccess) {
+            set_error_detail("radix sort launch", e);
+            return BT_ERR_CUDA;
+        }
+        q = dq;
+        qidx = di;
+    }
+    const DescendArgs a{&t, q, qidx, nq, d_out_vals, d_out_found, nullptr, &model->dev, nullptr};
+    e = descend_any(a, s);
+    if (e != cudaSuccess) {
+        set_error_detail("learned descent launch", e);
         return BT_ERR_CUDA;
     }
     return BT_OK;

