@@ -306,13 +306,22 @@ def _time_calls(fn, steps, flush, stream):
 def learned_leg(a, bt, flush, stream):
     """Plain level-wise search against the learned leaf predictor (PL with
     256 segments, MLP 1-32-32-1) on 2^24 keys from a mixture of three
-    lognormals, fanout 32, 90% hits, batches of 1024 and 2^20."""
-    import torch
+    lognormals (the configured workload) and, for contrast, 2^24 uniform
+    keys; fanout 32, 90% hits, batches of 1024 and 2^20."""
     n = 1 << 24
-    keys = W.lognormal_mixture_keys(n, seed=W.SEED_BASE + 4)
+    out = {}
+    for label, keys in (("lognormal", lambda: W.lognormal_mixture_keys(n, seed=W.SEED_BASE + 4)),
+                        ("uniform", lambda: W.uniform_keys(n, 64, seed=W.SEED_BASE + 2))):
+        out[label] = _learned_case(bt, flush, stream, keys(), label)
+    return out
+
+
+def _learned_case(bt, flush, stream, keys, label):
+    import torch
+    n = keys.size
     vals = W.rank_values(n, 64)
     tree = bt.BTree(keys, vals, 32)
-    res = {"workload": f"{n} lognormal-mixture uint64 keys (sigma 1, 2, 0.5), fanout 32, 90% hits"}
+    res = {"workload": f"{n} {label} uint64 keys, fanout 32, 90% hits"}
     t0 = time.perf_counter()
     pl = bt.bt_model_train(tree.handle, bt.BT_MODEL_PL, segments=256)
     t_pl = time.perf_counter() - t0

@@ -319,6 +319,7 @@ typedef struct bt_tune {
     uint32_t fanout;          /* m the tree was built with */
     uint32_t warps_per_block; /* descent blocks: 4, 8 or 16 warps */
     uint32_t pin_bytes;       /* budget for top levels kept in shared memory (0..49152) */
+    uint32_t staging;         /* BT_STAGE_CP_ASYNC or BT_STAGE_BULK */
     float us_per_batch;       /* median time of the sample batch with these settings */
 } bt_tune;
 
@@ -326,11 +327,24 @@ typedef struct bt_tune {
  * searches running on it).  BT_ERR_ARG on unsupported values. */
 bt_status bt_tree_set_launch(bt_tree *tree, uint32_t warps_per_block, uint32_t pin_bytes);
 
+/* How the descent stages node blocks into shared memory: BT_STAGE_CP_ASYNC
+ * (each lane copies 16-byte pieces) or BT_STAGE_BULK (one asynchronous bulk
+ * copy per node block, the GPU's copy engine (TMA), counted on an mbarrier
+ * with a bounded wait).  Results are identical; speed differs. */
+#define BT_STAGE_CP_ASYNC 0
+#define BT_STAGE_BULK 1
+bt_status bt_tree_set_staging(bt_tree *tree, uint32_t mode);
+
+/* BT_ERR_TIMEOUT if a bounded device wait of a search gave up since the
+ * last call (the results of such a search are invalid), else BT_OK; clears
+ * the counter.  Synchronous. */
+bt_status bt_check_timeouts(void);
+
 /*
  * bt_autotune -- build the tree at every fanout in {8, 16, 32, 64} and time
  * a sample batch (d_sample, nsample device queries) through bt_search_batch
  * for every combination of warps per block {4, 8, 16} and pinned bytes
- * {0, 16384, 49152}; keep the fastest.  *out receives the tree built with
+ * {0, 16384, 49152} and both staging modes; keep the fastest.  *out receives the tree built with
  * the best fanout and launch parameters applied, *best the choice and its
  * time.  Synchronizes `stream`.  Errors: as bt_build, plus BT_ERR_ARG.
  */
@@ -407,9 +421,10 @@ bt_status bt_server_run_trace(bt_server *server, uint64_t n, const double *t_arr
  * Learned leaf predictor.  Not in the paper: an extension in which a small
  * fp32 model, fitted or trained on the GPU on the tree's own (stored key,
  * leaf index) pairs, predicts a key's leaf directly so the search can skip
- * the inner levels.  The model's maximum error over the stored keys -- the
- * same device code computes it -- bounds a window of leaves around the
- * prediction; the window's boundaries are checked with exact integer
+ * the inner levels.  The model's maximum error over the stored keys, kept
+ * per range of predicted leaf (BT_ERR_RANGES ranges; the same device code
+ * computes it), bounds a window of leaves around each prediction; the
+ * window's boundaries are checked with exact integer
  * compares against the leaves' largest keys, and a warp any of whose queries
  * is not proven to lie in its window takes the plain level-wise descent.
  * Results are therefore always exactly those of bt_search_batch.
@@ -461,6 +476,13 @@ bt_status bt_model_get_info(const bt_model *model, bt_model_info *out);
  * inv_w[S], slope[S], icpt[S] (float), 20*S bytes; MLP: BT_MLP_PARAMS
  * floats.  BT_ERR_ARG if `bytes` is too small. */
 bt_status bt_model_copy_params(const bt_model *model, void *h_dst, uint64_t bytes);
+
+/* The error bound per range of prediction: entry r is the largest
+ * |leaf_hat - leaf| over the stored keys whose leaf_hat lies in
+ * [r*L/BT_ERR_RANGES, (r+1)*L/BT_ERR_RANGES); the search uses the bound of
+ * each query's own range.  h_dst needs n >= BT_ERR_RANGES entries. */
+#define BT_ERR_RANGES 256
+bt_status bt_model_copy_err_bounds(const bt_model *model, uint32_t *h_dst, uint32_t n);
 
 /* Mean-squared-error gradient of an MLP over n given samples, the training
  * kernel's own forward and backward pass: writes d_grad[BT_MLP_PARAMS] and

@@ -152,6 +152,17 @@ def max_error(leaf_hat: np.ndarray, leaf: np.ndarray) -> int:
     return int(np.max(np.abs(leaf_hat.astype(np.int64) - leaf.astype(np.int64)))) if leaf.size else 0
 
 
+def range_errors(leaf_hat: np.ndarray, leaf: np.ndarray, L: int, ranges: int = 256) -> np.ndarray:
+    """Largest |leaf_hat - leaf| per range r of leaf_hat, where range r holds
+    leaf_hat in [r*L/ranges, (r+1)*L/ranges)."""
+    h = leaf_hat.astype(np.int64)
+    r = (h * ranges) // L
+    d = np.abs(h - leaf.astype(np.int64))
+    out = np.zeros(ranges, np.int64)
+    np.maximum.at(out, r, d)
+    return out
+
+
 def window_leaf(leaf_max: np.ndarray, q, leaf_hat, err: int):
     """The leaf whose key range holds q, searched only in the window
     [leaf_hat - err, leaf_hat + err]; -1 where q's leaf lies outside it

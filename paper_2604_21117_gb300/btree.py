@@ -35,8 +35,10 @@ EXPORTED = ("bt_build", "bt_free", "bt_tree_info", "bt_tree_copy_image", "bt_sea
             "bt_search_host_workspace_bytes",
             "bt_search_batch_host", "bt_search_batch_noalloc", "bt_status_str", "bt_last_error_detail",
             "bt_model_train", "bt_model_free", "bt_model_get_info", "bt_model_copy_params", "bt_mlp_grad",
-            "bt_learned_descend_sorted", "bt_learned_search_batch", "bt_forest_create", "bt_forest_free",
-            "bt_forest_workspace_bytes", "bt_forest_search", "bt_tree_set_launch", "bt_autotune",
+            "bt_learned_descend_sorted", "bt_learned_search_batch", "bt_model_copy_err_bounds",
+            "bt_forest_create", "bt_forest_free",
+            "bt_forest_workspace_bytes", "bt_forest_search", "bt_tree_set_launch", "bt_tree_set_staging",
+            "bt_check_timeouts", "bt_autotune",
             "bt_server_create", "bt_server_submit", "bt_server_poll", "bt_server_drain", "bt_server_get_stats",
             "bt_server_destroy", "bt_server_run_trace")
 
@@ -293,6 +295,17 @@ def bt_model_copy_params(model: int):
     return out
 
 
+BT_ERR_RANGES = 256
+_lib.bt_model_copy_err_bounds.restype = _i
+_lib.bt_model_copy_err_bounds.argtypes = [_vp, _vp, ctypes.c_uint32]
+
+
+def bt_model_copy_err_bounds(model: int) -> np.ndarray:
+    out = np.zeros(BT_ERR_RANGES, np.uint32)
+    _check("bt_model_copy_err_bounds", _lib.bt_model_copy_err_bounds(model, out.ctypes.data, out.size))
+    return out
+
+
 def bt_mlp_grad(d_params, d_x, d_t, n: int, d_grad, d_loss, stream=None) -> None:
     _check("bt_mlp_grad", _lib.bt_mlp_grad(_dptr(d_params), _dptr(d_x), _dptr(d_t), n, _dptr(d_grad),
                                            _dptr(d_loss), _stream_handle(stream)))
@@ -318,7 +331,7 @@ class bt_batch_desc(ctypes.Structure):
 
 class bt_tune(ctypes.Structure):
     _fields_ = [("fanout", ctypes.c_uint32), ("warps_per_block", ctypes.c_uint32), ("pin_bytes", ctypes.c_uint32),
-                ("us_per_batch", ctypes.c_float)]
+                ("staging", ctypes.c_uint32), ("us_per_batch", ctypes.c_float)]
 
 
 BATCH_DESC_DTYPE = np.dtype([("tree", np.uint32), ("count", np.uint32), ("offset", np.uint64)])
@@ -333,6 +346,10 @@ _lib.bt_forest_search.restype = _i
 _lib.bt_forest_search.argtypes = [_vp, _vp, ctypes.c_uint32, _vp, _vp, _vp, _vp, _u64, ctypes.c_uint32, _vp]
 _lib.bt_tree_set_launch.restype = _i
 _lib.bt_tree_set_launch.argtypes = [_vp, ctypes.c_uint32, ctypes.c_uint32]
+_lib.bt_tree_set_staging.restype = _i
+_lib.bt_tree_set_staging.argtypes = [_vp, ctypes.c_uint32]
+_lib.bt_check_timeouts.restype = _i
+_lib.bt_check_timeouts.argtypes = []
 _lib.bt_autotune.restype = _i
 _lib.bt_autotune.argtypes = [_vp, _vp, _u64, _i, _i, _vp, _u64, _vp, ctypes.POINTER(_vp), ctypes.POINTER(bt_tune)]
 
@@ -362,6 +379,19 @@ def bt_forest_search(forest: int, d_batches, nbatches: int, d_queries, d_out_val
 
 def bt_tree_set_launch(tree: int, warps_per_block: int, pin_bytes: int) -> None:
     _check("bt_tree_set_launch", _lib.bt_tree_set_launch(tree, warps_per_block, pin_bytes))
+
+
+BT_STAGE_CP_ASYNC = 0
+BT_STAGE_BULK = 1
+
+
+def bt_tree_set_staging(tree: int, mode: int) -> None:
+    _check("bt_tree_set_staging", _lib.bt_tree_set_staging(tree, mode))
+
+
+def bt_check_timeouts() -> None:
+    """Raises if a bounded device wait of a search gave up since the last call."""
+    _check("bt_check_timeouts", _lib.bt_check_timeouts())
 
 
 def bt_autotune(h_keys: np.ndarray, h_vals: np.ndarray, d_sample, nsample: int, stream=None):

@@ -32,6 +32,7 @@ struct DevTree {
     int pin_levels;      // top levels copied to shared memory by the descent
     uint32_t pin_bytes;  // bytes from the root's block to the end of those levels
     int warps;           // warps per descent block
+    int staging;         // 0: 16-byte cp.async per lane, 1: one bulk copy (TMA) per node block
 };
 
 // Whole top levels (never the leaves) whose bytes fit `budget`, root first.

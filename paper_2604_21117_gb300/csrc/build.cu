@@ -62,6 +62,13 @@ extern "C" bt_status bt_tree_set_launch(bt_tree *t, uint32_t warps_per_block, ui
     return BT_OK;
 }
 
+extern "C" bt_status bt_tree_set_staging(bt_tree *t, uint32_t mode)
+{
+    if (!t || mode > 1) return BT_ERR_ARG;
+    t->dev.staging = static_cast<int>(mode);
+    return BT_OK;
+}
+
 extern "C" const char *bt_last_error_detail(void) { return g_detail; }
 
 extern "C" const char *bt_status_str(bt_status s)

@@ -260,9 +260,14 @@ __global__ void k_adam(float *__restrict__ p, float *__restrict__ g, float *__re
 
 // ------------------------------------------------------ error bound
 
+// Largest |leaf_hat - leaf| over every stored key, overall (err[0]) and per
+// range of leaf_hat (errs[]), by the same prediction code the search uses.
 template <typename K>
-__global__ void k_model_err(const DevTree t, ModelDev md, uint32_t *__restrict__ err)
+__global__ void k_model_err(const DevTree t, ModelDev md, uint32_t *__restrict__ err, uint32_t *__restrict__ errs)
 {
+    __shared__ uint32_t se[kErrRanges];
+    for (uint32_t i = threadIdx.x; i < kErrRanges; i += blockDim.x) se[i] = 0;
+    __syncthreads();
     const int lv = t.height - 1;
     const uint64_t n = t.cbase[lv] * t.nodes[lv] + t.crem[lv];
     uint32_t e = 0;
@@ -273,9 +278,13 @@ __global__ void k_model_err(const DevTree t, ModelDev md, uint32_t *__restrict__
         const uint32_t hat = model_leaf(md, md.b, md.inv_w, md.slope, md.icpt, md.mlp, key);
         const uint32_t d = hat > leaf ? hat - static_cast<uint32_t>(leaf) : static_cast<uint32_t>(leaf) - hat;
         e = d > e ? d : e;
+        if (d) atomicMax(&se[err_range(hat, md.leaves)], d);
     }
     e = __reduce_max_sync(0xffffffffu, e);
     if ((threadIdx.x & 31) == 0) atomicMax(err, e);
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < kErrRanges; i += blockDim.x)
+        if (se[i]) atomicMax(errs + i, se[i]);
 }
 
 static bt_status cuda_fail(const char *what, cudaError_t e)
@@ -329,9 +338,9 @@ static bt_status train_impl(const bt_tree *tree, const bt_learn_opts *o, cudaStr
         if (e != cudaSuccess) return cuda_fail("loss read", e);
     }
     uint32_t *err = reinterpret_cast<uint32_t *>(static_cast<unsigned char *>(mdl->d_mem));
-    e = cudaMemsetAsync(err, 0, sizeof(uint32_t), s);
+    e = cudaMemsetAsync(err, 0, 256 + kErrRanges * sizeof(uint32_t), s);
     if (e != cudaSuccess) return cuda_fail("error word reset", e);
-    k_model_err<K><<<grid, 256, 0, s>>>(t, md, err);
+    k_model_err<K><<<grid, 256, 0, s>>>(t, md, err, const_cast<uint32_t *>(md.errs));
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail("model kernels launch", e);
     uint32_t h_err = 0;
@@ -372,7 +381,7 @@ extern "C" bt_status bt_model_train(const bt_tree *tree, const bt_learn_opts *op
     memset(m, 0, sizeof(*m));
     // device memory: err word | leaf_max | model arrays
     const uint64_t kb = t.key_bytes;
-    uint64_t off = 256;
+    uint64_t off = 256 + kErrRanges * 4;  // err word, then the per-range bounds
     const uint64_t off_lmax = off;
     off = a256(off + L * kb);
     uint64_t off_b = 0, off_inv = 0, off_slope = 0, off_icpt = 0, off_mlp = 0;
@@ -401,6 +410,7 @@ extern "C" bt_status bt_model_train(const bt_tree *tree, const bt_learn_opts *op
     md.segments = S;
     md.leaves = static_cast<uint32_t>(L);
     md.leaf_max = base + off_lmax;
+    md.errs = reinterpret_cast<const uint32_t *>(base + 256);
     md.kmin = t.kmin;
     md.kmax = t.kmax;
     md.inv_range = (t.kmax > t.kmin) ? static_cast<float>(1.0 / static_cast<double>(t.kmax - t.kmin)) : 0.0f;
@@ -460,6 +470,14 @@ extern "C" bt_status bt_model_copy_params(const bt_model *m, void *h_dst, uint64
         e = cudaMemcpy(d, md.mlp, kMlpParams * 4ull, cudaMemcpyDeviceToHost);
     }
     if (e != cudaSuccess) return cuda_fail("model parameter copy", e);
+    return BT_OK;
+}
+
+extern "C" bt_status bt_model_copy_err_bounds(const bt_model *m, uint32_t *h_dst, uint32_t n)
+{
+    if (!m || !h_dst || n < kErrRanges) return BT_ERR_ARG;
+    const cudaError_t e = cudaMemcpy(h_dst, m->dev.errs, kErrRanges * sizeof(uint32_t), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail("error bound copy", e);
     return BT_OK;
 }
 

@@ -34,11 +34,22 @@ constexpr int kOffW1 = 0, kOffB1 = 32, kOffW2 = 64, kOffB2 = 64 + 1024, kOffW3 =
 
 enum ModelKind : int { kModelNone = 0, kModelPL = 1, kModelMLP = 2 };
 
+// The error bound is kept per range of predicted leaf: range r covers
+// leaf_hat in [r*L/kErrRanges, (r+1)*L/kErrRanges).  A stored key with
+// prediction leaf_hat lies within errs[range(leaf_hat)] leaves of it.
+constexpr uint32_t kErrRanges = 256;
+
+__host__ __device__ __forceinline__ uint32_t err_range(uint32_t hat, uint32_t L)
+{
+    return static_cast<uint32_t>((static_cast<uint64_t>(hat) * kErrRanges) / L);
+}
+
 // Everything the search kernel needs to use a model, passed by value.
 struct ModelDev {
     int kind;
     uint32_t segments;      // PL
     uint32_t err;           // max |leaf_hat - leaf| over the stored keys
+    const uint32_t *errs;   // the same maximum per range of leaf_hat (kErrRanges ranges)
     uint32_t leaves;        // L
     const uint64_t *b;      // PL breakpoints (as uint64 whatever the key width)
     const float *inv_w;     // PL

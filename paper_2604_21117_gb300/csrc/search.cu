@@ -48,6 +48,49 @@ __device__ __forceinline__ void cp_async_wait_all()
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
+// ---- bulk asynchronous copies (TMA, non-tensor form) with an mbarrier ----
+
+// Bounded waits that gave up (the results of that search are invalid);
+// read and cleared by bt_check_timeouts.
+__device__ unsigned int g_bt_timeouts;
+constexpr uint32_t kMbarSpinLimit = 1u << 22;
+
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned phase)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
 __device__ __forceinline__ unsigned lanemask_lt()
 {
     unsigned r;
@@ -76,10 +119,11 @@ constexpr int stage_slots()
     return (M * static_cast<int>(sizeof(K)) >= 512) ? 8 : 16;
 }
 
+// Shared memory per warp: its stage slots, its node list and its mbarrier.
 template <typename K, int M>
 constexpr int desc_smem_per_warp()
 {
-    return stage_slots<K, M>() * M * static_cast<int>(sizeof(K)) + 32 * 4;
+    return stage_slots<K, M>() * M * static_cast<int>(sizeof(K)) + 32 * 4 + 8;
 }
 
 // Number of slots of a node block holding a key smaller than `key`: the
@@ -161,6 +205,12 @@ __global__ void __launch_bounds__(kDescWarpsMax * 32) k_descend(
     unsigned char *after_stage = msm + mbytes + nw * SLOTS * M * sizeof(K);
     uint32_t *list = reinterpret_cast<uint32_t *>(after_stage) + warp * 32;
     K *lmstage = reinterpret_cast<K *>(after_stage + nw * 32 * 4) + warp * kLeafMaxCap;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(after_stage + nw * 32 * 4 +
+                                                  (LEARN ? nw * kLeafMaxCap * sizeof(K) : 0)) + warp;
+    const bool tma = (t.staging == 1);  // stage node blocks with bulk copies (else 16-byte cp.async)
+    uint32_t phase = 0;
+    if (tma && lane == 0) mbar_init(mbar);
+    __syncwarp();
 
     // Top levels, pinned once per block.
     const unsigned char *top = static_cast<const unsigned char *>(t.keys[0]);
@@ -236,8 +286,9 @@ __global__ void __launch_bounds__(kDescWarpsMax * 32) k_descend(
             // the query.  One unproven lane sends the warp down the tree.
             const uint32_t L = md.leaves;
             const uint32_t hat = model_leaf(md, mb, minv, mslope, micpt, mmlp, static_cast<uint64_t>(key));
-            const uint32_t lo = hat > md.err ? hat - md.err : 0u;
-            const uint32_t hi = (static_cast<uint64_t>(hat) + md.err < L) ? hat + md.err : L - 1;
+            const uint32_t er = __ldg(md.errs + err_range(hat, L));  // bound of this prediction's range
+            const uint32_t lo = hat > er ? hat - er : 0u;
+            const uint32_t hi = (static_cast<uint64_t>(hat) + er < L) ? hat + er : L - 1;
             uint32_t wlo = __reduce_min_sync(0xffffffffu, lo);
             if (wlo > 0) --wlo;
             const uint32_t whi = __reduce_max_sync(0xffffffffu, hi);
@@ -296,17 +347,43 @@ __global__ void __launch_bounds__(kDescWarpsMax * 32) k_descend(
             for (int rb = 0; rb < U; rb += SLOTS) {
                 const int nu = (U - rb < SLOTS) ? U - rb : SLOTS;
                 // Stage each distinct node's key block once.
-                for (int i = lane; i < nu * CH; i += 32) {
-                    const int u = i / CH, part = i - u * CH;
-                    const unsigned char *src = reinterpret_cast<const unsigned char *>(
-                                                   lk + static_cast<uint64_t>(list[rb + u]) * M) + part * 16;
-                    unsigned char *dp = reinterpret_cast<unsigned char *>(stage + u * M) + part * 16;
-                    if (last)
-                        cp_async16_cg(dp, src);
-                    else
-                        cp_async16_ca(dp, src);
+                if (tma) {
+                    // one bulk copy per node block, completion counted in bytes
+                    // on the warp's mbarrier; the wait is bounded
+                    constexpr unsigned kBlk = M * sizeof(K);
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    if (lane == 0) mbar_arrive_expect_tx(mbar, static_cast<unsigned>(nu) * kBlk);
+                    __syncwarp();
+                    if (lane < nu)
+                        bulk_g2s(stage + lane * M, lk + static_cast<uint64_t>(list[rb + lane]) * M, kBlk, mbar);
+                    bool gave_up = false;
+                    for (uint32_t spins = 0; !mbar_try_wait(mbar, phase);)
+                        if (++spins > kMbarSpinLimit) {
+                            gave_up = true;
+                            break;
+                        }
+                    if (__any_sync(0xffffffffu, gave_up)) {
+                        // record it, give the copies in flight a second bounded
+                        // wait to land, and leave: this warp's results are invalid
+                        if (lane == 0) atomicAdd(&g_bt_timeouts, 1u);
+                        for (uint32_t spins = 0; spins < kMbarSpinLimit && !mbar_try_wait(mbar, phase); ++spins) {
+                        }
+                        return;
+                    }
+                    phase ^= 1u;
+                } else {
+                    for (int i = lane; i < nu * CH; i += 32) {
+                        const int u = i / CH, part = i - u * CH;
+                        const unsigned char *src = reinterpret_cast<const unsigned char *>(
+                                                       lk + static_cast<uint64_t>(list[rb + u]) * M) + part * 16;
+                        unsigned char *dp = reinterpret_cast<unsigned char *>(stage + u * M) + part * 16;
+                        if (last)
+                            cp_async16_cg(dp, src);
+                        else
+                            cp_async16_ca(dp, src);
+                    }
+                    cp_async_wait_all();
                 }
-                cp_async_wait_all();
                 __syncwarp();
                 if (slot >= rb && slot < rb + nu) {
                     const K *blk = stage + (slot - rb) * M;
@@ -821,4 +898,19 @@ extern "C" bt_status bt_learned_search_batch(const bt_tree *tree, const bt_model
         return BT_ERR_CUDA;
     }
     return BT_OK;
+}
+
+extern "C" bt_status bt_check_timeouts(void)
+{
+    unsigned int v = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(&v, g_bt_timeouts, sizeof(v));
+    if (e == cudaSuccess && v) {
+        const unsigned int zero = 0;
+        e = cudaMemcpyToSymbol(g_bt_timeouts, &zero, sizeof(zero));
+    }
+    if (e != cudaSuccess) {
+        set_error_detail("timeout counter", e);
+        return BT_ERR_CUDA;
+    }
+    return v ? BT_ERR_TIMEOUT : BT_OK;
 }

@@ -102,18 +102,38 @@ def test_forest_search_replays_from_a_cuda_graph(bt):
     bt.bt_forest_free(forest)
 
 
-@pytest.mark.parametrize("warps,pin", [(4, 0), (16, 0), (4, 49152), (16, 49152), (8, 16384)])
-def test_launch_settings_do_not_change_results(bt, warps, pin):
+@pytest.mark.parametrize("warps,pin,staging", [(4, 0, 0), (16, 0, 0), (4, 49152, 0), (16, 49152, 0),
+                                               (8, 16384, 0), (4, 0, 1), (16, 49152, 1), (8, 16384, 1)])
+def test_launch_settings_do_not_change_results(bt, warps, pin, staging):
     keys = W.uniform_keys(500_000, 64, seed=63)
     vals = W.rank_values(keys.size, 64)
     tree = bt.BTree(keys, vals, 16)
     o = OracleTree(keys, vals, 16)
     bt.bt_tree_set_launch(tree.handle, warps, pin)
+    bt.bt_tree_set_staging(tree.handle, staging)
     q = W.make_queries(keys, 70_001, 0.9, seed=64, width_bits=64)
     import torch
     v, f = tree.search(torch.from_numpy(q).cuda())
+    bt.bt_check_timeouts()
     ov, of, _, _ = o.search(q)
     assert np.array_equal(v.cpu().numpy(), ov) and np.array_equal(f.cpu().numpy(), of)
+
+
+@pytest.mark.parametrize("fanout,key_bits", [(8, 32), (8, 64), (32, 32), (64, 64), (64, 32)])
+def test_bulk_staging_every_block_size(bt, fanout, key_bits):
+    """Bulk copies of every node-block size (8 slots of 4 bytes up to 64 of 8)."""
+    import torch
+    keys = W.uniform_keys(300_000, key_bits, seed=68 + fanout)
+    vals = W.rank_values(keys.size, 32)
+    tree = bt.BTree(keys, vals, fanout)
+    bt.bt_tree_set_staging(tree.handle, bt.BT_STAGE_BULK)
+    o = OracleTree(keys, vals, fanout)
+    q = W.make_queries(keys, 40_003, 0.7, seed=69, width_bits=key_bits)
+    for sb in (-1, 0):
+        v, f = tree.search(torch.from_numpy(q).cuda(), sort_bits=sb)
+        bt.bt_check_timeouts()
+        ov, of, _, _ = o.search(q)
+        assert np.array_equal(v.cpu().numpy(), ov) and np.array_equal(f.cpu().numpy(), of)
 
 
 def test_autotune_returns_a_correct_tree(bt):
@@ -124,7 +144,7 @@ def test_autotune_returns_a_correct_tree(bt):
     h, best = bt.bt_autotune(keys, vals, torch.from_numpy(sample).cuda(), sample.size)
     tree = bt.BTree(None, None, handle=h)
     assert best.fanout in (8, 16, 32, 64) and best.warps_per_block in (4, 8, 16)
-    assert best.pin_bytes in (0, 16384, 49152) and best.us_per_batch > 0
+    assert best.pin_bytes in (0, 16384, 49152) and best.staging in (0, 1) and best.us_per_batch > 0
     assert tree.fanout == best.fanout
     o = OracleTree(keys, vals, best.fanout)
     q = W.make_queries(keys, 30_000, 0.8, seed=67, width_bits=64)

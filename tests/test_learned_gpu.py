@@ -46,6 +46,7 @@ def test_pl_fit_matches_oracle_and_error_bound_is_exact(bt, dist):
     hat = LO.pl_predict(b, inv_w, slope, icpt, keys, L)
     info = bt.bt_model_get_info(mdl)
     assert info.max_err == LO.max_error(hat, leaf)
+    assert np.array_equal(bt.bt_model_copy_err_bounds(mdl).astype(np.int64), LO.range_errors(hat, leaf, L))
     bt.bt_model_free(mdl)
 
 

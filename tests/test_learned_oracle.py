@@ -102,6 +102,18 @@ def test_mlp_x_normalisation():
     assert list(x) == [0.0, 0.0, np.float32(0.5), np.float32(1.0), np.float32(1.0)]
 
 
+def test_range_errors_brute_force():
+    g = W.rng(9)
+    L = 1000
+    leaf = g.integers(0, L, 5000)
+    hat = np.clip(leaf + g.integers(-30, 31, 5000), 0, L - 1)
+    got = LO.range_errors(hat, leaf, L, 16)
+    for r in range(16):
+        sel = [abs(int(h) - int(l)) for h, l in zip(hat, leaf) if r * L <= int(h) * 16 < (r + 1) * L]
+        assert got[r] == (max(sel) if sel else 0)
+    assert got.max() == LO.max_error(hat, leaf)
+
+
 def test_window_leaf_and_max_error_brute_force():
     leaf_max = np.array([10, 20, 30, 40, 50], np.uint64)
     q = np.array([5, 15, 35, 45, 60, 30], np.uint64)
