@@ -147,6 +147,73 @@ def make_queries(keys: np.ndarray, nq: int, hit_frac: float, seed: int, width_bi
     return out.astype(dt)
 
 
+def _sort_rows(a: np.ndarray) -> np.ndarray:
+    """Rows of a (n, kb) uint8 array in lexicographic byte order, duplicates dropped."""
+    if a.shape[0] == 0:
+        return a
+    order = np.lexsort(a.T[::-1])
+    a = a[order]
+    keep = np.ones(a.shape[0], bool)
+    keep[1:] = np.any(a[1:] != a[:-1], axis=1)
+    return a[keep]
+
+
+def byte_keys(n: int, kb: int, seed: int, prefix_bytes: int = 0) -> np.ndarray:
+    """n distinct kb-byte keys as an (n, kb) uint8 array in lexicographic
+    order: `prefix_bytes` leading bytes shared by every key (drawn once),
+    the rest uniform random bytes."""
+    if n > 256 ** min(kb - prefix_bytes, 8) // 4:
+        raise ValueError("too few free bytes for n distinct keys")
+    g = rng(seed)
+    prefix = g.integers(0, 256, size=prefix_bytes, dtype=np.uint8)
+    out = np.empty((0, kb), np.uint8)
+    while out.shape[0] < n:
+        d = g.integers(0, 256, size=(n - out.shape[0] + 16, kb), dtype=np.uint8)
+        d[:, :prefix_bytes] = prefix
+        out = _sort_rows(np.concatenate([out, d]))
+    if out.shape[0] > n:
+        out = out[np.sort(g.choice(out.shape[0], n, replace=False))]
+    return np.ascontiguousarray(out)
+
+
+def make_byte_queries(keys: np.ndarray, nq: int, hit_frac: float, seed: int,
+                      zipf_s: float | None = None) -> np.ndarray:
+    """nq kb-byte queries, an (nq, kb) uint8 array: about hit_frac of them
+    copies of stored keys (uniform or Zipf(s) over a random key permutation),
+    the rest random rows sharing the keys' first byte distribution that are
+    not stored keys."""
+    g = rng(seed)
+    n, kb = keys.shape
+    out = np.empty((nq, kb), np.uint8)
+    if nq == 0:
+        return out
+    is_hit = g.random(nq) < (hit_frac if n else 0.0)
+    nh = int(is_hit.sum())
+    if nh:
+        if zipf_s is None:
+            idx = g.integers(0, n, size=nh)
+        else:
+            idx = g.permutation(n)[zipf_ranks(n, zipf_s, nh, g) - 1]
+        out[is_hit] = keys[idx]
+    nm = nq - nh
+    if nm:
+        stored = {bytes(r) for r in keys} if n <= 4_000_000 else None
+        miss = g.integers(0, 256, size=(nm, kb), dtype=np.uint8)
+        if n:
+            # keep the keys' leading bytes so that misses land inside the key range
+            src = keys[g.integers(0, n, size=nm)]
+            lead = g.integers(0, kb // 2 + 1, size=nm)
+            for i in range(nm):
+                miss[i, :lead[i]] = src[i, :lead[i]]
+        if stored is not None:
+            for i in range(nm):
+                while bytes(miss[i]) in stored:
+                    miss[i, -1] ^= 0x5A
+                    miss[i, -2] = g.integers(0, 256)
+        out[~is_hit] = miss
+    return out
+
+
 def log_uniform_batch_sizes(count: int, seed: int, lo: int = 1, hi: int = 1024) -> np.ndarray:
     """floor(exp(U(ln lo, ln hi))) clamped to [lo, hi]."""
     g = rng(seed)
