@@ -4,7 +4,7 @@
 Workload (default): one static tree of 2^24 distinct uniform uint64 keys,
 fanout 32, uint64 rank values; batches of 2^20 point lookups at 90% hits
 (uniform).  One step = one pass of the whole search path over one batch:
-the on-device radix sort of the batch, then the level-wise descent, leaf
+the on-device partition of the batch by key, then the level-wise descent, leaf
 probe and scatter to input order.  Inputs are resident in HBM when a step
 starts; L2 is flushed (a 256 MB device write) before every timed step.
 
@@ -54,6 +54,9 @@ def parse_args(argv=None):
     p.add_argument("--hit", type=float, default=0.9)
     p.add_argument("--zipf", type=float, default=None)
     p.add_argument("--sort-bits", type=int, default=-1)
+    p.add_argument("--staging", type=int, default=0, help="node staging: 0 = 16-byte cp.async, 1 = bulk copy")
+    p.add_argument("--warps", type=int, default=0, help="descent warps per block (0 = library default)")
+    p.add_argument("--pin", type=int, default=-1, help="pinned top-level bytes (-1 = library default)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true", help="skip e2e / small-batch latency legs")
     p.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain leg")
@@ -553,6 +556,9 @@ def run_ours(a):
     pool = 4
     batches = make_batches(a, keys, pool, rank)
     tree = bt.BTree(keys, vals, a.fanout)
+    bt.bt_tree_set_staging(tree.handle, a.staging)
+    if a.warps > 0 or a.pin >= 0:
+        bt.bt_tree_set_launch(tree.handle, a.warps if a.warps > 0 else 8, a.pin if a.pin >= 0 else 16384)
     m, kb, vb, B = a.fanout, 8, 8, a.batch
 
     alg = []
@@ -638,6 +644,7 @@ def run_ours(a):
         "config": {"workload": workload_name(a), "keys": a.keys, "fanout": m, "batch": B,
                    "hit_frac": a.hit, "query_dist": "uniform" if a.zipf is None else f"zipf{a.zipf}",
                    "sort_bits": "auto" if sort_bits < 0 else sort_bits,
+                   "staging": "bulk" if a.staging == 1 else "cp.async",
                    "l2": "flushed before every timed step (256 MB device write)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "p50_us": 1e3 * sdev[len(sdev) // 2], "p99_us": 1e3 * sdev[min(len(sdev) - 1, int(0.99 * len(sdev)))],

@@ -75,6 +75,10 @@ typedef struct bt_info {
     uint64_t level_key_offset[BT_MAX_LEVELS]; /* byte offset of the level's key blocks */
     uint64_t leaf_val_offset;              /* byte offset of the leaf value blocks */
     uint64_t device_bytes;                 /* size of the device image */
+    uint64_t split_offset;                 /* byte offset of the partition splitters */
+    uint64_t split_inv_offset;             /* byte offset of their fp32 segment reciprocals */
+    uint32_t nsplit;                       /* number of splitters (0..1023) */
+    uint32_t reserved;
     const void *d_image;                   /* device address of the image (read-only) */
 } bt_info;
 
@@ -103,7 +107,12 @@ typedef struct bt_info {
  * leaves a block of m value slots per leaf; every level array starts on a
  * 256-byte boundary, so blocks of 128 bytes or more start on a 128-byte line.
  * Unused key slots hold all-ones and are excluded from leaf matches by the
- * leaf's key count, so the all-ones key itself is legal.
+ * leaf's key count, so the all-ones key itself is legal.  After the values
+ * (each 256-byte aligned): the batch partition's splitters, nsplit =
+ * min(L - 1, 1023) keys, splitter j the largest key of leaf
+ * floor((j + 1) L / (nsplit + 1)) - 1; then nsplit + 1 fp32 values,
+ * 1 / (hi - lo + 1) for each key segment (lo, hi] the splitters bound
+ * (segment 0 starts at the smallest key, the last ends at the largest).
  *
  * Errors: BT_ERR_ARG, BT_ERR_FANOUT, BT_ERR_UNSORTED, BT_ERR_DUPLICATE,
  * BT_ERR_NOMEM, BT_ERR_CUDA.  *out is set only on BT_OK.

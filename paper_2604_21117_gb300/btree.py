@@ -50,6 +50,8 @@ class bt_info(ctypes.Structure):
                 ("level_nodes", ctypes.c_uint64 * BT_MAX_LEVELS),
                 ("level_key_offset", ctypes.c_uint64 * BT_MAX_LEVELS),
                 ("leaf_val_offset", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64),
+                ("split_offset", ctypes.c_uint64), ("split_inv_offset", ctypes.c_uint64),
+                ("nsplit", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
                 ("d_image", ctypes.c_void_p)]
 
 

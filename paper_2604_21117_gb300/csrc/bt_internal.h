@@ -33,6 +33,12 @@ struct DevTree {
     uint32_t pin_bytes;  // bytes from the root's block to the end of those levels
     int warps;           // warps per descent block
     int staging;         // 0: 16-byte cp.async per lane, 1: one bulk copy (TMA) per node block
+    // Splitters of the batch partition: the largest keys of nsplit evenly
+    // spaced leaves, and nsplit + 1 reciprocal widths of the key segments
+    // they bound (part_sort.cuh).
+    const void *split;
+    const float *split_inv;
+    uint32_t nsplit;
 };
 
 // Whole top levels (never the leaves) whose bytes fit `budget`, root first.

@@ -147,7 +147,17 @@ extern "C" bt_status bt_build(const void *h_keys, const void *h_vals, uint64_t n
         off = align_up(off + N * m * kb, 256);
     }
     t->info.leaf_val_offset = off;
-    if (h > 0) off = align_up(off + up[0] * m * vb, 256);
+    uint32_t nsplit = 0;
+    if (h > 0) {
+        off = align_up(off + up[0] * m * vb, 256);
+        nsplit = static_cast<uint32_t>(up[0] - 1 < 1023 ? up[0] - 1 : 1023);
+        t->info.split_offset = off;
+        off = align_up(off + static_cast<uint64_t>(nsplit) * kb, 256);
+        t->info.split_inv_offset = off;
+        off = align_up(off + (static_cast<uint64_t>(nsplit) + 1) * 4, 256);
+    }
+    t->info.nsplit = nsplit;
+    d.nsplit = nsplit;
     t->info.device_bytes = off;
 
     // Descent launch defaults: 8 warps per block, top levels up to 16 KB
@@ -198,6 +208,18 @@ extern "C" bt_status bt_build(const void *h_keys, const void *h_vals, uint64_t n
             first += cnt;
         }
     }
+    // Partition splitters and the reciprocal widths of the segments they bound.
+    {
+        void *sk = img + t->info.split_offset;
+        float *sinv = reinterpret_cast<float *>(img + t->info.split_inv_offset);
+        for (uint32_t j = 0; j < nsplit; ++j)
+            store_uint(sk, j, kb, node_max[(static_cast<uint64_t>(j) + 1) * L / (nsplit + 1) - 1]);
+        for (uint32_t c = 0; c <= nsplit; ++c) {
+            const uint64_t lo = c ? load_uint(sk, c - 1, kb) : d.kmin;
+            const uint64_t hi = c < nsplit ? load_uint(sk, c, kb) : d.kmax;
+            sinv[c] = static_cast<float>(1.0 / (static_cast<double>(hi - lo) + 1.0));
+        }
+    }
     // Inner levels bottom-up: separator j = largest key under child j.
     for (int l = leaf - 1; l >= 0; --l) {
         const uint64_t N = d.nodes[l];
@@ -234,6 +256,8 @@ extern "C" bt_status bt_build(const void *h_keys, const void *h_vals, uint64_t n
     for (int l = 0; l < h; ++l)
         d.keys[l] = static_cast<unsigned char *>(t->d_image) + t->info.level_key_offset[l];
     d.vals = static_cast<unsigned char *>(t->d_image) + t->info.leaf_val_offset;
+    d.split = static_cast<unsigned char *>(t->d_image) + t->info.split_offset;
+    d.split_inv = reinterpret_cast<const float *>(static_cast<unsigned char *>(t->d_image) + t->info.split_inv_offset);
     t->info.d_image = t->d_image;
     *out = t;
     return BT_OK;

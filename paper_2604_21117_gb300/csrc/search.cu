@@ -1,9 +1,9 @@
 // Batched level-wise B+ tree point search on GB300 (sm_103a).
 //
 // One search is (Sec. IV-A, IV-F):
-//   1. an on-device LSD radix sort of (query, input position) pairs on the
-//      leading bits of the normalised query key, so that queries routed to the
-//      same node end up adjacent (the paper's sorted batch);
+//   1. an on-device partition of (query, input position) pairs by a bucket
+//      number monotone in the key (part_sort.cuh), so that queries routed
+//      to the same node end up adjacent (the paper's sorted batch);
 //   2. the level-wise descent: each warp takes 32 consecutive queries of the
 //      sorted batch and walks them down the tree together; at every level it
 //      finds the distinct nodes its queries need (warp match/ballot/popc, the
@@ -25,7 +25,7 @@
 #include <cstring>
 
 #include "bt_internal.h"
-#include "radix_sort.cuh"
+#include "part_sort.cuh"
 
 namespace btgb {
 
@@ -432,40 +432,26 @@ __global__ void k_fill_miss(V *__restrict__ out_v, uint8_t *__restrict__ out_f, 
 
 static inline uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
 
-static inline uint32_t sort_tiles(uint64_t nq) { return static_cast<uint32_t>((nq + kSortTile - 1) / kSortTile); }
-
 struct WsLayout {
-    uint64_t qa, ia, qb, ib, counts, total;
+    uint64_t qb, ib, counts, total;
 };
 
-// Largest distribution width for a batch: about nq / tile buckets, at most
-// 2^12 buckets and at most kMaxBucketTiles (bucket, tile) pairs.
-static int dist_bits_max(uint64_t nq)
-{
-    const uint64_t ntiles = (nq + kSortTile - 1) / kSortTile;
-    int db = 0;
-    while (db < kMaxDistBits && (static_cast<uint64_t>(kSortTile) << db) < nq &&
-           (ntiles << (db + 1)) <= kMaxBucketTiles)
-        ++db;
-    return db;
-}
+// Bucket counters of the partition: at most 2^kMaxPartBits buckets, plus
+// the ticket word, rounded to whole 16-byte groups.
+constexpr uint64_t kPartCountWords = (1ull << kMaxPartBits) + 4;
 
-// Workspace: two (query, position) buffers -- the distribution's output and
-// the sorted batch -- then the distribution's [bucket][tile] count matrix.
+// Workspace: the partitioned batch (queries, then input positions) and the
+// partition's bucket counters.
 static WsLayout ws_layout(int kb, uint64_t nq)
 {
     WsLayout w;
     uint64_t o = 0;
-    w.qa = o;
-    o = align256(o + nq * kb);
-    w.ia = o;
-    o = align256(o + nq * 4);
     w.qb = o;
     o = align256(o + nq * kb);
     w.ib = o;
     o = align256(o + nq * 4);
     w.counts = o;
-    o = align256(o + (static_cast<uint64_t>(sort_tiles(nq)) << dist_bits_max(nq)) * 4);
+    o = align256(o + kPartCountWords * 4);
     w.total = nq ? o : 0;
     return w;
 }
@@ -474,8 +460,13 @@ static int bitlen(uint64_t x) { return x ? 64 - __builtin_clzll(x) : 0; }
 
 // Queries per batch from which the sort pays for itself by node reuse.
 constexpr uint64_t kAutoSortMinBatch = 16384;
-// Bits ordered within a tile below the distribution's bucket bits.
-constexpr int kAutoLocalBits = 8;
+// Automatic bucket bits: about 16 queries per bucket, so that a warp's 32
+// consecutive queries span about two buckets.
+static int auto_part_bits(uint64_t nq)
+{
+    const int b = bitlen(nq) - 5;
+    return b < 1 ? 1 : (b > kMaxPartBits ? kMaxPartBits : b);
+}
 
 // One search's descent launch: everything a kernel instantiation needs.
 struct DescendArgs {
@@ -582,75 +573,79 @@ __global__ void k_copy_identity(const K *__restrict__ q, K *__restrict__ qo, uin
     }
 }
 
-// The two-stage sort of (query, position) pairs into (dst_q, dst_i): the
-// distribution into workspace buffer A (skipped when dbits == 0), then the
-// per-tile local sort from A (or from the queries) into the destination.
-template <typename K>
-static cudaError_t radix_sort(const K *q, uint64_t nq, const SortNorm &sn, unsigned char *ws,
-                              const WsLayout &w, K *dst_q, uint32_t *dst_i, cudaStream_t s)
+// Partition parameters for a tree and batch: how c (the splitter count
+// below the query) and the interpolation bits r make a bucket of `bits` bits.
+struct PartPlan {
+    int bits;       // 0: no partition
+    int r;          // interpolation bits inside a splitter segment
+    int cshift;     // right shift of c when bits < the splitter bits
+    uint32_t nb;    // buckets, rounded up to a multiple of 4
+};
+
+// sort_bits < 0: auto_part_bits for batches of at least kAutoSortMinBatch
+// queries, else none; sort_bits > 0: that many bits, at most kMaxPartBits.
+static PartPlan plan_partition(const DevTree &t, int32_t sort_bits, uint64_t nq)
 {
-    const uint32_t ntiles = sort_tiles(nq);
-    cudaError_t e;
-    const K *src_q = q;
-    const uint32_t *src_i = nullptr;
-    if (sn.dbits > 0) {
-        const uint32_t nb = 1u << sn.dbits;
-        uint32_t *counts = reinterpret_cast<uint32_t *>(ws + w.counts);
-        constexpr int msmem = msd_smem_bytes<K>();
-        static const cudaError_t attr =
-            cudaFuncSetAttribute(k_msd_scatter<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, msmem);
-        if (attr != cudaSuccess) return attr;
-        K *qa = reinterpret_cast<K *>(ws + w.qa);
-        uint32_t *ia = reinterpret_cast<uint32_t *>(ws + w.ia);
-        k_msd_hist<K><<<ntiles, kSortThreads, 0, s>>>(q, nq, sn, counts, ntiles);
-        k_msd_offsets<<<1, 1024, 0, s>>>(counts, nb * ntiles);
-        k_msd_scatter<K><<<ntiles, kSortThreads, msmem, s>>>(q, nq, sn, counts, ntiles, qa, ia);
-        src_q = qa;
-        src_i = ia;
+    PartPlan p{0, 0, 0, 0};
+    int bits = sort_bits;
+    if (bits < 0) bits = (nq >= kAutoSortMinBatch) ? auto_part_bits(nq) : 0;
+    if (bits > kMaxPartBits) bits = kMaxPartBits;
+    if (bits <= 0 || t.height == 0) return p;
+    const int cbits = bitlen(t.nsplit);  // c is in [0, nsplit]
+    p.bits = bits;
+    p.r = bits > cbits ? bits - cbits : 0;
+    p.cshift = cbits > bits ? cbits - bits : 0;
+    const uint64_t nb = ((static_cast<uint64_t>(t.nsplit) >> p.cshift) + 1) << p.r;
+    p.nb = static_cast<uint32_t>((nb + 3) / 4 * 4);
+    return p;
+}
+
+template <typename K>
+static cudaError_t part_sort(const DevTree &t, const K *q, uint64_t nq, const PartPlan &pp, unsigned char *ws,
+                             const WsLayout &w, K *dst_q, uint32_t *dst_i, cudaStream_t s)
+{
+    PartNorm<K> pn;
+    pn.split = static_cast<const K *>(t.split);
+    pn.split_inv = t.split_inv;
+    pn.kmin = static_cast<K>(t.kmin);
+    pn.nsplit = t.nsplit;
+    pn.r = pp.r;
+    pn.cshift = pp.cshift;
+    pn.scale = static_cast<float>(1u << pp.r);
+    uint32_t *counts = reinterpret_cast<uint32_t *>(ws + w.counts);
+    cudaError_t e = cudaMemsetAsync(counts, 0, (static_cast<uint64_t>(pp.nb) + 4) * 4, s);
+    if (e != cudaSuccess) return e;
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
     }
-    constexpr int lsmem = local_smem_bytes<K>();
-    static const cudaError_t lattr =
-        cudaFuncSetAttribute(k_local_sort<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, lsmem);
-    if (lattr != cudaSuccess) return lattr;
-    k_local_sort<K><<<ntiles, kSortThreads, lsmem, s>>>(src_q, src_i, dst_q, dst_i, nq, sn);
+    uint64_t grid = (nq + kPartThreads * kPartUnroll - 1) / (kPartThreads * kPartUnroll);
+    const uint64_t cap = 2ull * sms;  // two blocks of 1024 threads per SM
+    if (grid > cap) grid = cap;
+    k_part_count<K><<<static_cast<unsigned>(grid), kPartThreads, 0, s>>>(q, nq, pn, counts, pp.nb);
+    k_part_scatter<K><<<static_cast<unsigned>(grid), kPartThreads, 0, s>>>(q, nq, pn, counts, dst_q, dst_i);
     return cudaGetLastError();
 }
 
-// Where bt_search_batch puts the sorted batch: workspace buffer B.
+// Where bt_search_batch puts the partitioned batch.
 static void internal_sort_dst(unsigned char *ws, const WsLayout &w, void **dq, uint32_t **di)
 {
     *dq = ws + w.qb;
     *di = reinterpret_cast<uint32_t *>(ws + w.ib);
 }
 
-static cudaError_t sort_any(const DevTree &t, const void *q, uint64_t nq, const SortNorm &sn,
+static cudaError_t sort_any(const DevTree &t, const void *q, uint64_t nq, const PartPlan &pp,
                             unsigned char *ws, const WsLayout &w, void *dq, uint32_t *di,
                             cudaStream_t s)
 {
     if (t.key_bytes == 8)
-        return radix_sort<uint64_t>(static_cast<const uint64_t *>(q), nq, sn, ws, w,
-                                    static_cast<uint64_t *>(dq), di, s);
-    return radix_sort<uint32_t>(static_cast<const uint32_t *>(q), nq, sn, ws, w,
-                                static_cast<uint32_t *>(dq), di, s);
-}
-
-// Sort parameters for this tree and batch.  sort_bits < 0: kAutoLocalBits
-// bits within tiles below the distribution's bucket bits, for batches of at
-// least kAutoSortMinBatch queries, else no sort.  sort_bits > 0: that many
-// leading bits within tiles (capped at the key range and width).
-static SortNorm make_norm(const DevTree &t, int32_t sort_bits, uint64_t nq)
-{
-    SortNorm sn{t.kmin, t.kmax - t.kmin, 0, 0, 0};
-    sn.rl = bitlen(sn.range);
-    const int db = dist_bits_max(nq);
-    int bits = sort_bits;
-    if (bits < 0) bits = (nq >= kAutoSortMinBatch) ? db + kAutoLocalBits : 0;
-    if (bits > sn.rl) bits = sn.rl;
-    if (bits > 8 * t.key_bytes) bits = 8 * t.key_bytes;
-    if (bits <= 0) return sn;
-    sn.bits = bits;
-    sn.dbits = db < bits ? db : bits;
-    return sn;
+        return part_sort<uint64_t>(t, static_cast<const uint64_t *>(q), nq, pp, ws, w,
+                                   static_cast<uint64_t *>(dq), di, s);
+    return part_sort<uint32_t>(t, static_cast<const uint32_t *>(q), nq, pp, ws, w,
+                               static_cast<uint32_t *>(dq), di, s);
 }
 
 }  // namespace btgb
@@ -661,9 +656,7 @@ extern "C" int32_t bt_sort_launches(const bt_tree *tree, uint64_t nq, int32_t so
 {
     if (!tree) return -1;
     if (tree->dev.height == 0 || nq == 0) return 0;
-    const SortNorm sn = make_norm(tree->dev, sort_bits, nq);
-    if (sn.bits == 0) return 0;
-    return sn.dbits > 0 ? 4 : 1;
+    return plan_partition(tree->dev, sort_bits, nq).bits ? 2 : 0;
 }
 
 extern "C" uint64_t bt_search_workspace_bytes(const bt_tree *tree, uint64_t nq)
@@ -709,17 +702,17 @@ extern "C" bt_status bt_search_batch_ex(const bt_tree *tree, const void *d_queri
         return BT_OK;
     }
 
-    const SortNorm sn = make_norm(t, opts ? opts->sort_bits : -1, nq);
+    const PartPlan pp = plan_partition(t, opts ? opts->sort_bits : -1, nq);
     const void *q = d_queries;
     const uint32_t *qidx = nullptr;
     unsigned char *ws = static_cast<unsigned char *>(d_workspace);
-    if (sn.bits > 0) {
+    if (pp.bits > 0) {
         void *dq;
         uint32_t *di;
         internal_sort_dst(ws, w, &dq, &di);
-        e = sort_any(t, d_queries, nq, sn, ws, w, dq, di, s);
+        e = sort_any(t, d_queries, nq, pp, ws, w, dq, di, s);
         if (e != cudaSuccess) {
-            set_error_detail("radix sort launch", e);
+            set_error_detail("batch partition launch", e);
             return BT_ERR_CUDA;
         }
         q = dq;
@@ -789,9 +782,9 @@ extern "C" bt_status bt_sort_batch(const bt_tree *tree, const void *d_queries, u
     if (!d_workspace || ws_bytes < w.total || (reinterpret_cast<uintptr_t>(d_workspace) & 255u))
         return BT_ERR_WORKSPACE;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    const SortNorm sn = make_norm(t, sort_bits, nq);
+    const PartPlan pp = plan_partition(t, sort_bits, nq);
     cudaError_t e;
-    if (sn.bits == 0) {
+    if (pp.bits == 0) {
         const unsigned grid = static_cast<unsigned>((nq + 255) / 256 < 4096 ? (nq + 255) / 256 : 4096);
         if (t.key_bytes == 8)
             k_copy_identity<uint64_t><<<grid, 256, 0, s>>>(static_cast<const uint64_t *>(d_queries),
@@ -803,11 +796,11 @@ extern "C" bt_status bt_sort_batch(const bt_tree *tree, const void *d_queries, u
                                                            d_sorted_index, nq);
         e = cudaGetLastError();
     } else {
-        e = sort_any(t, d_queries, nq, sn, static_cast<unsigned char *>(d_workspace), w, d_sorted_queries,
+        e = sort_any(t, d_queries, nq, pp, static_cast<unsigned char *>(d_workspace), w, d_sorted_queries,
                      d_sorted_index, s);
     }
     if (e != cudaSuccess) {
-        set_error_detail("radix sort launch", e);
+        set_error_detail("batch partition launch", e);
         return BT_ERR_CUDA;
     }
     return BT_OK;
@@ -874,18 +867,18 @@ extern "C" bt_status bt_learned_search_batch(const bt_tree *tree, const bt_model
     if (!d_workspace || ws_bytes < w.total || (reinterpret_cast<uintptr_t>(d_workspace) & 255u))
         return BT_ERR_WORKSPACE;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    const SortNorm sn = make_norm(t, -1, nq);
+    const PartPlan pp = plan_partition(t, -1, nq);
     const void *q = d_queries;
     const uint32_t *qidx = nullptr;
     unsigned char *ws = static_cast<unsigned char *>(d_workspace);
     cudaError_t e;
-    if (sn.bits > 0) {
+    if (pp.bits > 0) {
         void *dq;
         uint32_t *di;
         internal_sort_dst(ws, w, &dq, &di);
-        e = sort_any(t, d_queries, nq, sn, ws, w, dq, di, s);
+        e = sort_any(t, d_queries, nq, pp, ws, w, dq, di, s);
         if (e != cudaSuccess) {
-            set_error_detail("radix sort launch", e);
+            set_error_detail("batch partition launch", e);
             return BT_ERR_CUDA;
         }
         q = dq;

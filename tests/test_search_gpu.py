@@ -237,35 +237,47 @@ def _sorted(bt, tree, q, sb):
     return sq, si, sq.cpu().numpy(), si.cpu().numpy().view(np.uint32)
 
 
-def _check_sort_contract(keys, q, hsq, hsi, sb, kw):
-    """A permutation with its keys, ordered on the leading D bucket bits
-    across the batch and on the leading `bits` bits within every aligned run
-    of 4096 positions."""
+def _splitters(bt, tree):
+    info = bt.bt_tree_info(tree.handle)
+    img = bt.bt_tree_copy_image(tree.handle, int(info.device_bytes))
+    kb = int(info.key_bytes)
+    dt = np.uint64 if kb == 8 else np.uint32
+    o = int(info.split_offset)
+    sp = img[o: o + int(info.nsplit) * kb].view(dt).astype(np.uint64)
+    return sp, int(info.nsplit)
+
+
+def _check_sort_contract(bt, tree, keys, q, hsq, hsi, sb):
+    """A permutation with its keys, ordered by a bucket number monotone in
+    the key: exactly ordered by splitter segment (the count of the tree's
+    splitters below the key), and inside a segment out of order only
+    between keys less than one interpolation bucket apart."""
     nq = q.size
     assert np.array_equal(np.sort(hsi), np.arange(nq, dtype=np.uint32))
     assert np.array_equal(hsq, q[hsi])
-    kmin, kmax = int(keys[0]), int(keys[-1])
-    rl = (kmax - kmin).bit_length()
-    ntiles = -(-nq // 4096)
-    d = 0  # distribution bits: ~nq/4096 buckets, <= 2^12, <= 2^20 (bucket, tile) pairs
-    while d < 12 and (4096 << d) < nq and (ntiles << (d + 1)) <= (1 << 20):
-        d += 1
-    bits = sb if sb > 0 else ((d + 8) if (sb < 0 and nq >= 16384) else 0)
-    bits = min(bits, rl, kw)
-    if bits <= 0:
+    bits = sb if sb > 0 else ((min(max((nq).bit_length() - 5, 1), 16)) if (sb < 0 and nq >= 16384) else 0)
+    bits = min(bits, 16)
+    if bits <= 0 or keys.size == 0:
         assert np.array_equal(hsi, np.arange(nq, dtype=np.uint32))
         return
-    d = min(d, bits)
-    nk = np.clip(hsq.astype(np.uint64), np.uint64(kmin), np.uint64(kmax)) - np.uint64(kmin)
-
-    def field(nb):
-        return nk >> np.uint64(max(rl - nb, 0)) if nb else np.zeros_like(nk)
-    fd = field(d)
-    assert np.all(fd[1:] >= fd[:-1])
-    fb = field(bits)
-    for s in range(0, nq, 4096):
-        t = fb[s:s + 4096]
-        assert np.all(t[1:] >= t[:-1]), s
+    sp, nsplit = _splitters(bt, tree)
+    cbits = nsplit.bit_length()
+    r, cshift = max(bits - cbits, 0), max(cbits - bits, 0)
+    k = hsq.astype(np.uint64)
+    c = np.searchsorted(sp, k, side="left")
+    assert np.all(np.diff(c >> cshift) >= 0)
+    if r == 0:
+        return
+    lo = np.concatenate([[int(keys[0])], sp.astype(object)]) if nsplit else np.array([int(keys[0])], object)
+    hi = np.concatenate([sp.astype(object), [int(keys[-1])]]) if nsplit else np.array([int(keys[-1])], object)
+    starts = np.flatnonzero(np.diff(c, prepend=-1))
+    ends = np.append(starts[1:], nq)
+    for s0, e0 in zip(starts, ends):
+        seg = int(c[s0])
+        bw = (int(hi[seg]) - int(lo[seg]) + 1) / (1 << r)
+        run = k[s0:e0].astype(np.float64)
+        back = np.maximum.accumulate(run) - run
+        assert back.max() <= bw * 1.01 + 2, (seg, back.max(), bw)
 
 
 @pytest.mark.parametrize("kw", [32, 64])
@@ -279,7 +291,7 @@ def test_split_sort_then_descend(bt, kw, sb):
     o = OracleTree(keys, vals, 32)
     q = W.make_queries(keys, 50_001, 0.9, seed=19, width_bits=kw, zipf_s=1.1)
     sq, si, hsq, hsi = _sorted(bt, tree, q, sb)
-    _check_sort_contract(keys, q, hsq, hsi, sb, kw)
+    _check_sort_contract(bt, tree, keys, q, hsq, hsi, sb)
     v, fo = tree.alloc_outputs(q.size)
     bt.bt_descend_sorted(tree.handle, sq, si, q.size, v, fo)
     ov, of, _, _ = o.search(q)
@@ -288,16 +300,17 @@ def test_split_sort_then_descend(bt, kw, sb):
 
 
 @pytest.mark.parametrize("dist", ["uniform", "zipf", "lognormal", "same"])
-@pytest.mark.parametrize("nq", [1, 4095, 4096, 4097, 100_000, 1 << 20])
+@pytest.mark.parametrize("nq", [1, 4095, 16383, 16384, 100_000, 1 << 20])
 def test_sort_contract_sizes_and_skew(bt, dist, nq):
-    """The distribution stage on skewed input (a hot key's bucket holds most
-    of the batch) and sizes around the tile boundary."""
+    """The partition on skewed input (a hot key's bucket holds most of the
+    batch), skewed keys (splitter segments follow the key distribution) and
+    sizes around the auto-partition threshold."""
     keys = W.lognormal_mixture_keys(300_000, seed=20) if dist == "lognormal" else W.uniform_keys(300_000, 64, seed=20)
     tree = bt.BTree(keys, W.rank_values(keys.size, 64), 32)
     if dist == "same":
         q = np.full(nq, keys[1234], np.uint64)
     else:
         q = W.make_queries(keys, nq, 0.9, seed=nq + 1, width_bits=64, zipf_s=1.1 if dist == "zipf" else None)
-    for sb in (-1, 16, 64):
+    for sb in (-1, 4, 16, 64):
         _, _, hsq, hsi = _sorted(bt, tree, q, sb)
-        _check_sort_contract(keys, q, hsq, hsi, sb, 64)
+        _check_sort_contract(bt, tree, keys, q, hsq, hsi, sb)
