@@ -42,7 +42,11 @@ struct CUstream_st;
 typedef struct CUstream_st *bt_stream;
 
 /* Width of keys and values in bytes. */
-typedef enum bt_width { BT_U32 = 4, BT_U64 = 8 } bt_width;
+/* Key and value widths.  BT_B32 (keys only) is the paper's 32-byte key
+ * (Sec. IV-B, IV-E): a string of 32 bytes compared byte by byte from the
+ * first, the first unequal byte deciding (lexicographic order, as memcmp);
+ * key arrays and query arrays hold 32 bytes per key. */
+typedef enum bt_width { BT_U32 = 4, BT_U64 = 8, BT_B32 = 32 } bt_width;
 
 typedef enum bt_status {
     BT_OK = 0,
@@ -90,7 +94,8 @@ typedef struct bt_info {
  *   h_vals   n values of val_w bytes, value i belongs to key i (host).
  *   n        number of keys; 0 builds an empty tree in which every query
  *            misses.  Every level must hold fewer than 2^32 nodes.
- *   key_w, val_w   BT_U32 or BT_U64.
+ *   key_w    BT_U32, BT_U64 or BT_B32.
+ *   val_w    BT_U32 or BT_U64.
  *   fanout   m in {8, 16, 32, 64}: inner nodes hold up to m children and
  *            m-1 separators, leaves up to m-1 keys (Sec. III).
  *   stream   stream for the one host-to-device copy; the call synchronizes
@@ -107,12 +112,18 @@ typedef struct bt_info {
  * leaves a block of m value slots per leaf; every level array starts on a
  * 256-byte boundary, so blocks of 128 bytes or more start on a 128-byte line.
  * Unused key slots hold all-ones and are excluded from leaf matches by the
- * leaf's key count, so the all-ones key itself is legal.  After the values
+ * leaf's key count, so the all-ones key itself is legal.  A 32-byte key
+ * slot holds four 64-bit words, most significant first, word j the
+ * big-endian value of key bytes 8j..8j+7 (comparing the words in order as
+ * unsigned integers compares the bytes lexicographically).  After the values
  * (each 256-byte aligned): the batch partition's splitters, nsplit =
  * min(L - 1, 1023) keys, splitter j the largest key of leaf
  * floor((j + 1) L / (nsplit + 1)) - 1; then nsplit + 1 fp32 values,
  * 1 / (hi - lo + 1) for each key segment (lo, hi] the splitters bound
- * (segment 0 starts at the smallest key, the last ends at the largest).
+ * (segment 0 starts at the smallest key, the last ends at the largest); for
+ * 32-byte keys lo and hi are the big-endian values of the 8 bytes after the
+ * p bytes the segment's bounds share (p <= 24), and nsplit + 1 bytes p
+ * follow.
  *
  * Errors: BT_ERR_ARG, BT_ERR_FANOUT, BT_ERR_UNSORTED, BT_ERR_DUPLICATE,
  * BT_ERR_NOMEM, BT_ERR_CUDA.  *out is set only on BT_OK.
@@ -301,7 +312,8 @@ typedef struct bt_batch_desc {
 typedef struct bt_forest bt_forest;
 
 /* A device table of `count` built trees with equal key and value widths
- * (fanouts may differ).  The trees must outlive the forest. */
+ * (fanouts may differ; integer keys only: BT_ERR_ARG for 32-byte keys).
+ * The trees must outlive the forest. */
 bt_status bt_forest_create(const bt_tree *const *trees, uint32_t count, bt_forest **out);
 void bt_forest_free(bt_forest *forest);
 
@@ -477,7 +489,8 @@ typedef struct bt_model_info {
 
 /* Fit (PL) or train (MLP) a model for `tree` on the GPU and compute its
  * error bound; synchronizes `stream`.  The model is only valid with this tree.
- * Errors: BT_ERR_ARG (empty tree, bad options), BT_ERR_NOMEM, BT_ERR_CUDA. */
+ * Integer keys only.
+ * Errors: BT_ERR_ARG (empty tree, 32-byte keys, bad options), BT_ERR_NOMEM, BT_ERR_CUDA. */
 bt_status bt_model_train(const bt_tree *tree, const bt_learn_opts *opts, bt_stream stream, bt_model **out);
 void bt_model_free(bt_model *model);
 bt_status bt_model_get_info(const bt_model *model, bt_model_info *out);

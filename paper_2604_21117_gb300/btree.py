@@ -23,7 +23,7 @@ if not os.path.exists(LIB_PATH):
 
 _lib = ctypes.CDLL(LIB_PATH)
 
-BT_U32, BT_U64 = 4, 8
+BT_U32, BT_U64, BT_B32 = 4, 8, 32
 BT_MAX_LEVELS = 24
 STATUS = {0: "BT_OK", 1: "BT_ERR_ARG", 2: "BT_ERR_UNSORTED", 3: "BT_ERR_DUPLICATE",
           4: "BT_ERR_FANOUT", 5: "BT_ERR_NOMEM", 6: "BT_ERR_CUDA", 7: "BT_ERR_TIMEOUT",
@@ -142,15 +142,21 @@ def bt_status_str(status: int) -> str:
 
 
 def bt_build(h_keys: np.ndarray, h_vals: np.ndarray, fanout: int, stream=None) -> int:
-    """Bulk-load a tree from sorted host keys/values; returns the opaque handle."""
+    """Bulk-load a tree from sorted host keys/values; returns the opaque handle.
+    Keys: a 1-D uint32/uint64 array, or an (n, 32) uint8 array of 32-byte keys."""
     k = np.ascontiguousarray(h_keys)
     v = np.ascontiguousarray(h_vals)
-    if k.shape != v.shape or k.ndim != 1:
-        raise ValueError("keys and values must be 1-D arrays of equal length")
+    if k.ndim == 2 and k.dtype == np.uint8 and k.shape[1] == 32:
+        n, kw = k.shape[0], BT_B32
+    elif k.ndim == 1:
+        n, kw = k.size, _width(k.dtype)
+    else:
+        raise ValueError("keys must be a 1-D uint32/uint64 array or an (n, 32) uint8 array")
+    if v.ndim != 1 or v.size != n:
+        raise ValueError("values must be a 1-D array with one value per key")
     out = _vp()
-    st = _lib.bt_build(k.ctypes.data if k.size else None, v.ctypes.data if v.size else None,
-                       k.size, _width(k.dtype), _width(v.dtype), fanout, _stream_handle(stream),
-                       ctypes.byref(out))
+    st = _lib.bt_build(k.ctypes.data if n else None, v.ctypes.data if n else None,
+                       n, kw, _width(v.dtype), fanout, _stream_handle(stream), ctypes.byref(out))
     _check("bt_build", st)
     return out.value
 
@@ -556,14 +562,19 @@ class BTree:
         f = torch.empty(nq, dtype=torch.uint8, device="cuda")
         return v, f
 
+    def count(self, queries) -> int:
+        """Queries in a batch: its elements, or its rows of 32 bytes for 32-byte keys."""
+        n = int(queries.numel() if hasattr(queries, "numel") else np.asarray(queries).size)
+        return n // 32 if self.key_bytes == 32 else n
+
     def search_into(self, d_queries, d_out_vals, d_out_found, d_workspace, ws_bytes: int,
                     sort_bits: int = -1, d_fetch_counts=None, stream=None):
-        bt_search_batch_ex(self.handle, d_queries, int(d_queries.numel()), d_out_vals, d_out_found,
+        bt_search_batch_ex(self.handle, d_queries, self.count(d_queries), d_out_vals, d_out_found,
                            d_workspace, ws_bytes, sort_bits, d_fetch_counts, stream)
 
     def search(self, d_queries, sort_bits: int = -1, stream=None):
         """Allocate outputs and workspace, search, return (values, found) CUDA tensors."""
-        nq = int(d_queries.numel())
+        nq = self.count(d_queries)
         v, f = self.alloc_outputs(nq)
         ws, nb = self.alloc_workspace(nq)
         self.search_into(d_queries, v, f, ws, nb, sort_bits=sort_bits, stream=stream)
@@ -572,7 +583,7 @@ class BTree:
     def search_host(self, h_queries: np.ndarray, stream=None):
         """Search from host memory through bt_search_batch_host; returns numpy arrays."""
         import torch
-        nq = int(h_queries.size)
+        nq = self.count(h_queries)
         vals = np.empty(nq, np.uint64 if self.val_bytes == 8 else np.uint32)
         found = np.empty(nq, np.uint8)
         ws, nb = self.alloc_workspace(nq, host=True)

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include "btree_gb300.h"
+#include "keys.cuh"
 #include "learned.cuh"
 
 namespace btgb {
@@ -25,7 +26,8 @@ struct DevTree {
     uint64_t cbase[BT_MAX_LEVELS];
     uint64_t crem[BT_MAX_LEVELS];
     const void *vals;                  // leaf value blocks, m slots per leaf
-    uint64_t kmin, kmax;               // smallest and largest key (sort normalisation)
+    uint64_t kmin, kmax;               // smallest and largest key (integer keys)
+    uint64_t kmin32[4], kmax32[4];     // the same for 32-byte keys, as Key32 words
     int height;
     int m;
     int key_bytes, val_bytes;
@@ -38,6 +40,7 @@ struct DevTree {
     // they bound (part_sort.cuh).
     const void *split;
     const float *split_inv;
+    const unsigned char *split_off;  // 32-byte keys: bytes shared within each segment
     uint32_t nsplit;
 };
 

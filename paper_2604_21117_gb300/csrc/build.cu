@@ -38,6 +38,46 @@ static inline void store_uint(void *p, uint64_t i, int bytes, uint64_t v)
 
 static inline uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
 
+// Big-endian value of 8 bytes.
+static inline uint64_t be64(const unsigned char *b)
+{
+    uint64_t v = 0;
+    for (int i = 0; i < 8; ++i) v = (v << 8) | b[i];
+    return v;
+}
+
+static inline const unsigned char *key_ptr(const void *h_keys, uint64_t i, int kb)
+{
+    return static_cast<const unsigned char *>(h_keys) + i * static_cast<uint64_t>(kb);
+}
+
+// Key i of the caller's array into device slot `slot` of a key array:
+// integers as they are, 32-byte keys as four big-endian 64-bit words.
+static inline void store_key(void *dst, uint64_t slot, int kb, const void *h_keys, uint64_t i)
+{
+    if (kb == 32) {
+        uint64_t *w = static_cast<uint64_t *>(dst) + slot * 4;
+        const unsigned char *b = key_ptr(h_keys, i, kb);
+        for (int j = 0; j < 4; ++j) w[j] = be64(b + 8 * j);
+    } else {
+        store_uint(dst, slot, kb, load_uint(h_keys, i, kb));
+    }
+}
+
+// All-ones padding slot (all-ones words for 32-byte keys).
+static inline void store_pad(void *dst, uint64_t slot, int kb)
+{
+    memset(static_cast<unsigned char *>(dst) + slot * static_cast<uint64_t>(kb), 0xFF, static_cast<size_t>(kb));
+}
+
+// <0, 0, >0 as key a is below, equal to or above key b.
+static inline int key_cmp(const void *h_keys, uint64_t a, uint64_t b, int kb)
+{
+    if (kb == 32) return memcmp(key_ptr(h_keys, a, kb), key_ptr(h_keys, b, kb), 32);
+    const uint64_t x = load_uint(h_keys, a, kb), y = load_uint(h_keys, b, kb);
+    return (x > y) - (x < y);
+}
+
 void set_pin_levels(DevTree &d, const bt_info &info, uint32_t budget)
 {
     d.pin_levels = 0;
@@ -91,7 +131,7 @@ extern "C" bt_status bt_build(const void *h_keys, const void *h_vals, uint64_t n
                               bt_width val_w, uint32_t fanout, bt_stream stream, bt_tree **out)
 {
     if (!out) return BT_ERR_ARG;
-    if ((key_w != BT_U32 && key_w != BT_U64) || (val_w != BT_U32 && val_w != BT_U64))
+    if ((key_w != BT_U32 && key_w != BT_U64 && key_w != BT_B32) || (val_w != BT_U32 && val_w != BT_U64))
         return BT_ERR_ARG;
     if (fanout != 8 && fanout != 16 && fanout != 32 && fanout != 64) return BT_ERR_FANOUT;
     if (n > 0 && (!h_keys || !h_vals)) return BT_ERR_ARG;
@@ -99,9 +139,9 @@ extern "C" bt_status bt_build(const void *h_keys, const void *h_vals, uint64_t n
     const uint64_t m = fanout, kmax_per_node = m - 1;
 
     for (uint64_t i = 1; i < n; ++i) {
-        uint64_t a = load_uint(h_keys, i - 1, kb), b = load_uint(h_keys, i, kb);
-        if (b < a) return BT_ERR_UNSORTED;
-        if (b == a) return BT_ERR_DUPLICATE;
+        const int c = key_cmp(h_keys, i - 1, i, kb);
+        if (c > 0) return BT_ERR_UNSORTED;
+        if (c == 0) return BT_ERR_DUPLICATE;
     }
 
     // Level sizes, leaves first.
@@ -132,7 +172,12 @@ extern "C" bt_status bt_build(const void *h_keys, const void *h_vals, uint64_t n
     t->info.key_bytes = static_cast<uint32_t>(kb);
     t->info.val_bytes = static_cast<uint32_t>(vb);
     t->info.n = n;
-    if (n > 0) {
+    if (n > 0 && kb == 32) {
+        for (int j = 0; j < 4; ++j) {
+            d.kmin32[j] = be64(key_ptr(h_keys, 0, kb) + 8 * j);
+            d.kmax32[j] = be64(key_ptr(h_keys, n - 1, kb) + 8 * j);
+        }
+    } else if (n > 0) {
         d.kmin = load_uint(h_keys, 0, kb);
         d.kmax = load_uint(h_keys, n - 1, kb);
     }
@@ -148,6 +193,7 @@ extern "C" bt_status bt_build(const void *h_keys, const void *h_vals, uint64_t n
     }
     t->info.leaf_val_offset = off;
     uint32_t nsplit = 0;
+    uint64_t split_off_offset = 0;
     if (h > 0) {
         off = align_up(off + up[0] * m * vb, 256);
         nsplit = static_cast<uint32_t>(up[0] - 1 < 1023 ? up[0] - 1 : 1023);
@@ -155,6 +201,10 @@ extern "C" bt_status bt_build(const void *h_keys, const void *h_vals, uint64_t n
         off = align_up(off + static_cast<uint64_t>(nsplit) * kb, 256);
         t->info.split_inv_offset = off;
         off = align_up(off + (static_cast<uint64_t>(nsplit) + 1) * 4, 256);
+        if (kb == 32) {
+            split_off_offset = off;
+            off = align_up(off + static_cast<uint64_t>(nsplit) + 1, 256);
+        }
     }
     t->info.nsplit = nsplit;
     d.nsplit = nsplit;
@@ -190,21 +240,20 @@ extern "C" bt_status bt_build(const void *h_keys, const void *h_vals, uint64_t n
     const uint64_t L = d.nodes[leaf];
     void *lk = img + t->info.level_key_offset[leaf];
     void *lv = img + t->info.leaf_val_offset;
-    const uint64_t pad = (kb == 8) ? ~0ull : 0xFFFFFFFFull;
-    std::vector<uint64_t> node_max(L);
+    std::vector<uint64_t> node_max(L);  // index of the largest key under each node
     {
         uint64_t first = 0;
         for (uint64_t i = 0; i < L; ++i) {
             const uint64_t cnt = d.cbase[leaf] + (i < d.crem[leaf] ? 1 : 0);
             for (uint64_t j = 0; j < m; ++j) {
                 if (j < cnt) {
-                    store_uint(lk, i * m + j, kb, load_uint(h_keys, first + j, kb));
+                    store_key(lk, i * m + j, kb, h_keys, first + j);
                     store_uint(lv, i * m + j, vb, load_uint(h_vals, first + j, vb));
                 } else {
-                    store_uint(lk, i * m + j, kb, pad);
+                    store_pad(lk, i * m + j, kb);
                 }
             }
-            node_max[i] = load_uint(h_keys, first + cnt - 1, kb);
+            node_max[i] = first + cnt - 1;
             first += cnt;
         }
     }
@@ -212,12 +261,25 @@ extern "C" bt_status bt_build(const void *h_keys, const void *h_vals, uint64_t n
     {
         void *sk = img + t->info.split_offset;
         float *sinv = reinterpret_cast<float *>(img + t->info.split_inv_offset);
-        for (uint32_t j = 0; j < nsplit; ++j)
-            store_uint(sk, j, kb, node_max[(static_cast<uint64_t>(j) + 1) * L / (nsplit + 1) - 1]);
+        std::vector<uint64_t> sidx(nsplit);  // key index of each splitter
+        for (uint32_t j = 0; j < nsplit; ++j) {
+            sidx[j] = node_max[(static_cast<uint64_t>(j) + 1) * L / (nsplit + 1) - 1];
+            store_key(sk, j, kb, h_keys, sidx[j]);
+        }
         for (uint32_t c = 0; c <= nsplit; ++c) {
-            const uint64_t lo = c ? load_uint(sk, c - 1, kb) : d.kmin;
-            const uint64_t hi = c < nsplit ? load_uint(sk, c, kb) : d.kmax;
-            sinv[c] = static_cast<float>(1.0 / (static_cast<double>(hi - lo) + 1.0));
+            const uint64_t lo = c ? sidx[c - 1] : 0, hi = c < nsplit ? sidx[c] : n - 1;
+            double width;
+            if (kb == 32) {
+                // 8 bytes after the bytes every key of the segment shares
+                const unsigned char *a = key_ptr(h_keys, lo, kb), *b = key_ptr(h_keys, hi, kb);
+                int p = 0;
+                while (p < 24 && a[p] == b[p]) ++p;
+                img[split_off_offset + c] = static_cast<unsigned char>(p);
+                width = static_cast<double>(be64(b + p) - be64(a + p));
+            } else {
+                width = static_cast<double>(load_uint(h_keys, hi, kb) - load_uint(h_keys, lo, kb));
+            }
+            sinv[c] = static_cast<float>(1.0 / (width + 1.0));
         }
     }
     // Inner levels bottom-up: separator j = largest key under child j.
@@ -228,8 +290,12 @@ extern "C" bt_status bt_build(const void *h_keys, const void *h_vals, uint64_t n
         uint64_t first = 0;
         for (uint64_t i = 0; i < N; ++i) {
             const uint64_t span = d.cbase[l] + (i < d.crem[l] ? 1 : 0);
-            for (uint64_t j = 0; j < m; ++j)
-                store_uint(ik, i * m + j, kb, (j + 1 < span) ? node_max[first + j] : pad);
+            for (uint64_t j = 0; j < m; ++j) {
+                if (j + 1 < span)
+                    store_key(ik, i * m + j, kb, h_keys, node_max[first + j]);
+                else
+                    store_pad(ik, i * m + j, kb);
+            }
             upper_max[i] = node_max[first + span - 1];
             first += span;
         }
@@ -258,6 +324,7 @@ extern "C" bt_status bt_build(const void *h_keys, const void *h_vals, uint64_t n
     d.vals = static_cast<unsigned char *>(t->d_image) + t->info.leaf_val_offset;
     d.split = static_cast<unsigned char *>(t->d_image) + t->info.split_offset;
     d.split_inv = reinterpret_cast<const float *>(static_cast<unsigned char *>(t->d_image) + t->info.split_inv_offset);
+    d.split_off = kb == 32 ? static_cast<unsigned char *>(t->d_image) + split_off_offset : nullptr;
     t->info.d_image = t->d_image;
     *out = t;
     return BT_OK;

@@ -215,7 +215,7 @@ extern "C" bt_status bt_forest_create(const bt_tree *const *trees, uint32_t coun
 {
     if (!trees || !out || count == 0) return BT_ERR_ARG;
     for (uint32_t i = 0; i < count; ++i)
-        if (!trees[i] || trees[i]->dev.key_bytes != trees[0]->dev.key_bytes ||
+        if (!trees[i] || trees[i]->dev.key_bytes == 32 || trees[i]->dev.key_bytes != trees[0]->dev.key_bytes ||
             trees[i]->dev.val_bytes != trees[0]->dev.val_bytes)
             return BT_ERR_ARG;
     bt_forest *f = new (std::nothrow) bt_forest;

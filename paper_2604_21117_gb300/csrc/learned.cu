@@ -363,7 +363,7 @@ extern "C" bt_status bt_model_train(const bt_tree *tree, const bt_learn_opts *op
 {
     if (!tree || !opts || !out) return BT_ERR_ARG;
     const DevTree &t = tree->dev;
-    if (t.height == 0) return BT_ERR_ARG;
+    if (t.height == 0 || t.key_bytes == 32) return BT_ERR_ARG;
     if (opts->kind != BT_MODEL_PL && opts->kind != BT_MODEL_MLP) return BT_ERR_ARG;
     const uint64_t n = tree->info.n;
     const uint64_t L = t.nodes[t.height - 1];

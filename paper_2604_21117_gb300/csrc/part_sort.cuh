@@ -14,7 +14,9 @@
 //          kSplitSlots of them, built with the tree), so c is q's rank among
 //          the keys to within one segment, whatever the key distribution;
 //     s  = q's position inside segment c on r bits, by linear interpolation
-//          between the segment's bounds (fp32; monotone in q).
+//          between the segment's bounds (fp32; monotone in q).  32-byte keys
+//          interpolate on the 8 bytes that follow the bytes the segment's
+//          bounds (hence all its keys) share.
 //
 //   k_part_count    per query: its bucket; warp-aggregated atomic counts
 //                   (equal buckets within a warp are counted once, so a hot
@@ -33,6 +35,8 @@
 
 #include <cstdint>
 
+#include "keys.cuh"
+
 namespace btgb {
 
 constexpr int kSplitSlots = 1023;   // splitters per tree, at most
@@ -46,7 +50,9 @@ template <typename K>
 struct PartNorm {
     const K *split;         // nsplit splitters, ascending (device)
     const float *split_inv; // nsplit + 1 reciprocal segment widths (device)
+    const unsigned char *split_off;  // 32-byte keys: per segment, bytes its keys share
     K kmin;                 // smallest key: lower bound of segment 0
+    K kmax;                 // largest key: upper bound of the last segment
     uint32_t nsplit;
     int r;                  // interpolation bits within a segment
     int cshift;             // with r == 0: bucket = c >> cshift (fewer bits than c has)
@@ -59,6 +65,7 @@ template <typename K>
 struct PartSmem {
     K sp[kSplitSlots + 1];
     float inv[kSplitSlots + 1];
+    unsigned char off[kSplitSlots + 1];
     uint32_t scan_tmp[32];
     uint32_t last;
 };
@@ -67,8 +74,9 @@ template <typename K>
 __device__ __forceinline__ void part_load_tables(PartSmem<K> &S, const PartNorm<K> &pn)
 {
     for (int i = threadIdx.x; i <= kSplitSlots; i += blockDim.x) {
-        S.sp[i] = i < static_cast<int>(pn.nsplit) ? pn.split[i] : static_cast<K>(~static_cast<K>(0));
+        S.sp[i] = i < static_cast<int>(pn.nsplit) ? pn.split[i] : KeyOps<K>::ones();
         S.inv[i] = i <= static_cast<int>(pn.nsplit) ? pn.split_inv[i] : 0.0f;
+        S.off[i] = (pn.split_off && i <= static_cast<int>(pn.nsplit)) ? pn.split_off[i] : 0;
     }
 }
 
@@ -84,6 +92,32 @@ __device__ __forceinline__ uint32_t part_bucket(const PartSmem<K> &S, const Part
     const float d = q > lo ? static_cast<float>(static_cast<uint64_t>(q - lo)) : 0.0f;
     const float top = pn.scale - 1.0f;
     const float x = fminf(__fmul_rn(__fmul_rn(d, S.inv[c]), pn.scale), top);
+    return (c << pn.r) | static_cast<uint32_t>(x);
+}
+
+// 8 bytes of a 32-byte key from byte p on (p <= 24), as a big-endian number.
+__device__ __forceinline__ uint64_t key32_window(const Key32 &k, int p)
+{
+    const int j = p >> 3, s = (p & 7) * 8;
+    const uint64_t hi = k.w[j];
+    const uint64_t lo = j < 3 ? k.w[j + 1] : 0ull;
+    return s ? (hi << s) | (lo >> (64 - s)) : hi;
+}
+
+__device__ __forceinline__ uint32_t part_bucket(const PartSmem<Key32> &S, const PartNorm<Key32> &pn, const Key32 &q)
+{
+    uint32_t c = 0;
+#pragma unroll
+    for (uint32_t h = (kSplitSlots + 1) / 2; h >= 1; h >>= 1)
+        if (S.sp[c + h - 1] < q) c += h;
+    if (pn.r == 0) return c >> pn.cshift;
+    const uint32_t top = (1u << pn.r) - 1u;
+    const Key32 lo = c ? S.sp[c - 1] : pn.kmin;
+    if (!(lo < q)) return c << pn.r;
+    if (c == pn.nsplit && pn.kmax < q) return (c << pn.r) | top;
+    const int p = S.off[c];
+    const float d = static_cast<float>(key32_window(q, p) - key32_window(lo, p));
+    const float x = fminf(__fmul_rn(__fmul_rn(d, S.inv[c]), pn.scale), static_cast<float>(top));
     return (c << pn.r) | static_cast<uint32_t>(x);
 }
 
@@ -122,7 +156,7 @@ __device__ __forceinline__ uint32_t part_block_excl_scan(uint32_t v, uint32_t *t
 // counts[0..nb) must be zero and counts[nb] (the ticket) zero on entry; on
 // exit counts[b] is the first position of bucket b.  nb is a multiple of 4.
 template <typename K>
-__global__ void __launch_bounds__(kPartThreads) k_part_count(const K *__restrict__ q, uint64_t nq, PartNorm<K> pn,
+__global__ void __launch_bounds__(kPartThreads) k_part_count(const RawOf<K> *__restrict__ q, uint64_t nq, PartNorm<K> pn,
                                                              uint32_t *__restrict__ counts, uint32_t nb)
 {
     __shared__ PartSmem<K> S;
@@ -132,7 +166,7 @@ __global__ void __launch_bounds__(kPartThreads) k_part_count(const K *__restrict
     const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
     for (uint64_t i0 = static_cast<uint64_t>(blockIdx.x) * blockDim.x + (threadIdx.x & ~31u); i0 < nq;
          i0 += stride * kPartUnroll) {
-        K key[kPartUnroll];
+        RawOf<K> key[kPartUnroll];
 #pragma unroll
         for (int u = 0; u < kPartUnroll; ++u) {
             const uint64_t i = i0 + u * stride + lane;
@@ -143,7 +177,7 @@ __global__ void __launch_bounds__(kPartThreads) k_part_count(const K *__restrict
             const uint64_t i = i0 + u * stride + lane;
             const unsigned vm = __ballot_sync(0xffffffffu, i < nq);
             if (i < nq) {
-                const uint32_t b = part_bucket(S, pn, key[u]);
+                const uint32_t b = part_bucket(S, pn, KeyOps<K>::from_raw(key[u]));
                 const unsigned same = __match_any_sync(vm, b);
                 if ((same & part_lanemask_lt()) == 0) atomicAdd(counts + b, static_cast<uint32_t>(__popc(same)));
             }
@@ -180,8 +214,9 @@ __global__ void __launch_bounds__(kPartThreads) k_part_count(const K *__restrict
 }
 
 template <typename K>
-__global__ void __launch_bounds__(kPartThreads) k_part_scatter(const K *__restrict__ q, uint64_t nq, PartNorm<K> pn,
-                                                               uint32_t *__restrict__ cursor, K *__restrict__ out_q,
+__global__ void __launch_bounds__(kPartThreads) k_part_scatter(const RawOf<K> *__restrict__ q, uint64_t nq,
+                                                               PartNorm<K> pn, uint32_t *__restrict__ cursor,
+                                                               RawOf<K> *__restrict__ out_q,
                                                                uint32_t *__restrict__ out_i)
 {
     __shared__ PartSmem<K> S;
@@ -191,7 +226,7 @@ __global__ void __launch_bounds__(kPartThreads) k_part_scatter(const K *__restri
     const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
     for (uint64_t i0 = static_cast<uint64_t>(blockIdx.x) * blockDim.x + (threadIdx.x & ~31u); i0 < nq;
          i0 += stride * kPartUnroll) {
-        K key[kPartUnroll];
+        RawOf<K> key[kPartUnroll];
 #pragma unroll
         for (int u = 0; u < kPartUnroll; ++u) {
             const uint64_t i = i0 + u * stride + lane;
@@ -202,7 +237,7 @@ __global__ void __launch_bounds__(kPartThreads) k_part_scatter(const K *__restri
             const uint64_t i = i0 + u * stride + lane;
             const unsigned vm = __ballot_sync(0xffffffffu, i < nq);
             if (i < nq) {
-                const uint32_t b = part_bucket(S, pn, key[u]);
+                const uint32_t b = part_bucket(S, pn, KeyOps<K>::from_raw(key[u]));
                 const unsigned same = __match_any_sync(vm, b);
                 const int leader = __ffs(same) - 1;
                 uint32_t base = 0;

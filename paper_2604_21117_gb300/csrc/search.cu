@@ -23,6 +23,7 @@
 
 #include <cstdint>
 #include <cstring>
+#include <type_traits>
 
 #include "bt_internal.h"
 #include "part_sort.cuh"
@@ -116,7 +117,7 @@ constexpr int kPinBudgetMax = 49152;
 template <typename K, int M>
 constexpr int stage_slots()
 {
-    return (M * static_cast<int>(sizeof(K)) >= 512) ? 8 : 16;
+    return (M * static_cast<int>(sizeof(K)) >= 2048) ? 4 : (M * static_cast<int>(sizeof(K)) >= 512) ? 8 : 16;
 }
 
 // Shared memory per warp: its stage slots, its node list and its mbarrier.
@@ -188,7 +189,7 @@ __host__ __device__ inline uint32_t model_smem_bytes(const ModelDev &m)
 
 template <typename K, typename V, int M, bool COUNT, bool LEARN>
 __global__ void __launch_bounds__(kDescWarpsMax * 32) k_descend(
-    const DevTree t, const K *__restrict__ q, const uint32_t *__restrict__ qidx, uint64_t nq,
+    const DevTree t, const RawOf<K> *__restrict__ q, const uint32_t *__restrict__ qidx, uint64_t nq,
     V *__restrict__ out_v, uint8_t *__restrict__ out_f, unsigned long long *__restrict__ fetch,
     const ModelDev md, unsigned long long *__restrict__ lstats)
 {
@@ -218,7 +219,8 @@ __global__ void __launch_bounds__(kDescWarpsMax * 32) k_descend(
     // The model's parameters, copied once per block when they fit.
     const uint64_t *mb = md.b;
     const float *minv = md.inv_w, *mslope = md.slope, *micpt = md.icpt, *mmlp = md.mlp;
-    if (LEARN && mbytes) {
+    if constexpr (LEARN) {
+      if (mbytes) {
         if (md.kind == kModelPL) {
             const uint32_t S = md.segments;
             uint64_t *sb = reinterpret_cast<uint64_t *>(msm);
@@ -238,6 +240,7 @@ __global__ void __launch_bounds__(kDescWarpsMax * 32) k_descend(
             for (uint32_t i = threadIdx.x; i < static_cast<uint32_t>(kMlpParams); i += blockDim.x) sp[i] = md.mlp[i];
             mmlp = sp;
         }
+      }
     }
     cp_async_wait_all();
     __syncthreads();
@@ -254,7 +257,7 @@ __global__ void __launch_bounds__(kDescWarpsMax * 32) k_descend(
     {
         const uint64_t pos = c * 32 + lane;
         const bool v = pos < nq;
-        key_n = q[v ? pos : c * 32];
+        key_n = KeyOps<K>::load(q, v ? pos : c * 32);
         dst_n = v ? (qidx ? qidx[pos] : static_cast<uint32_t>(pos)) : 0u;
     }
     // The previous chunk's result: its value load is issued at its leaf
@@ -272,13 +275,13 @@ __global__ void __launch_bounds__(kDescWarpsMax * 32) k_descend(
         if (cn < nchunks) {  // prefetch the next chunk
             const uint64_t pn = cn * 32 + lane;
             const bool vn = pn < nq;
-            key_n = q[vn ? pn : cn * 32];
+            key_n = KeyOps<K>::load(q, vn ? pn : cn * 32);
             dst_n = vn ? (qidx ? qidx[pn] : static_cast<uint32_t>(pn)) : 0u;
         }
 
         uint32_t node = 0;
         int l = 0;
-        if (LEARN) {
+        if constexpr (LEARN) {
             // Predicted leaf and its error window; the warp stages the leaf
             // maxima covering all its windows (plus the leaf below) and every
             // lane proves its leaf: the first window leaf whose largest key
@@ -520,7 +523,7 @@ static cudaError_t launch_descend(const DescendArgs &a, cudaStream_t s)
     uint64_t grid = (chunks + nw - 1) / nw;
     const uint64_t cap = static_cast<uint64_t>(sms) * occ_cache[nw][key];
     if (grid > cap) grid = cap;
-    kern<<<static_cast<unsigned>(grid), threads, smem, s>>>(*a.t, static_cast<const K *>(a.q), a.qidx, a.nq,
+    kern<<<static_cast<unsigned>(grid), threads, smem, s>>>(*a.t, static_cast<const RawOf<K> *>(a.q), a.qidx, a.nq,
                                                            static_cast<V *>(a.out_v), a.out_f, a.fetch, md,
                                                            a.lstats);
     return cudaGetLastError();
@@ -529,7 +532,9 @@ static cudaError_t launch_descend(const DescendArgs &a, cudaStream_t s)
 template <typename K, typename V, int M>
 static cudaError_t dispatch_mode(const DescendArgs &a, cudaStream_t s)
 {
-    if (a.md) return launch_descend<K, V, M, false, true>(a, s);
+    if constexpr (!std::is_same<K, Key32>::value) {
+        if (a.md) return launch_descend<K, V, M, false, true>(a, s);
+    }
     if (a.fetch) return launch_descend<K, V, M, true, false>(a, s);
     return launch_descend<K, V, M, false, false>(a, s);
 }
@@ -550,6 +555,10 @@ static cudaError_t descend_any(const DescendArgs &a, cudaStream_t s)
     if (a.t->key_bytes == 8) {
         if (a.t->val_bytes == 8) return dispatch_m<uint64_t, uint64_t>(a, s);
         return dispatch_m<uint64_t, uint32_t>(a, s);
+    }
+    if (a.t->key_bytes == 32) {
+        if (a.t->val_bytes == 8) return dispatch_m<Key32, uint64_t>(a, s);
+        return dispatch_m<Key32, uint32_t>(a, s);
     }
     if (a.t->val_bytes == 8) return dispatch_m<uint32_t, uint64_t>(a, s);
     return dispatch_m<uint32_t, uint32_t>(a, s);
@@ -601,13 +610,30 @@ static PartPlan plan_partition(const DevTree &t, int32_t sort_bits, uint64_t nq)
 }
 
 template <typename K>
-static cudaError_t part_sort(const DevTree &t, const K *q, uint64_t nq, const PartPlan &pp, unsigned char *ws,
-                             const WsLayout &w, K *dst_q, uint32_t *dst_i, cudaStream_t s)
+static void tree_bounds(const DevTree &t, K *lo, K *hi)
+{
+    *lo = static_cast<K>(t.kmin);
+    *hi = static_cast<K>(t.kmax);
+}
+
+template <>
+void tree_bounds<Key32>(const DevTree &t, Key32 *lo, Key32 *hi)
+{
+    for (int j = 0; j < 4; ++j) {
+        lo->w[j] = t.kmin32[j];
+        hi->w[j] = t.kmax32[j];
+    }
+}
+
+template <typename K>
+static cudaError_t part_sort(const DevTree &t, const RawOf<K> *q, uint64_t nq, const PartPlan &pp,
+                             unsigned char *ws, const WsLayout &w, RawOf<K> *dst_q, uint32_t *dst_i, cudaStream_t s)
 {
     PartNorm<K> pn;
     pn.split = static_cast<const K *>(t.split);
     pn.split_inv = t.split_inv;
-    pn.kmin = static_cast<K>(t.kmin);
+    pn.split_off = t.split_off;
+    tree_bounds<K>(t, &pn.kmin, &pn.kmax);
     pn.nsplit = t.nsplit;
     pn.r = pp.r;
     pn.cshift = pp.cshift;
@@ -641,6 +667,8 @@ static cudaError_t sort_any(const DevTree &t, const void *q, uint64_t nq, const 
                             unsigned char *ws, const WsLayout &w, void *dq, uint32_t *di,
                             cudaStream_t s)
 {
+    if (t.key_bytes == 32)
+        return part_sort<Key32>(t, static_cast<const Raw32 *>(q), nq, pp, ws, w, static_cast<Raw32 *>(dq), di, s);
     if (t.key_bytes == 8)
         return part_sort<uint64_t>(t, static_cast<const uint64_t *>(q), nq, pp, ws, w,
                                    static_cast<uint64_t *>(dq), di, s);
@@ -786,7 +814,10 @@ extern "C" bt_status bt_sort_batch(const bt_tree *tree, const void *d_queries, u
     cudaError_t e;
     if (pp.bits == 0) {
         const unsigned grid = static_cast<unsigned>((nq + 255) / 256 < 4096 ? (nq + 255) / 256 : 4096);
-        if (t.key_bytes == 8)
+        if (t.key_bytes == 32)
+            k_copy_identity<Raw32><<<grid, 256, 0, s>>>(static_cast<const Raw32 *>(d_queries),
+                                                        static_cast<Raw32 *>(d_sorted_queries), d_sorted_index, nq);
+        else if (t.key_bytes == 8)
             k_copy_identity<uint64_t><<<grid, 256, 0, s>>>(static_cast<const uint64_t *>(d_queries),
                                                            static_cast<uint64_t *>(d_sorted_queries),
                                                            d_sorted_index, nq);

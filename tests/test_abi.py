@@ -61,6 +61,27 @@ def test_build_rejects_bad_arguments_before_touching_the_gpu(bt):
         bt.bt_build(np.array([1, 2], np.int64), np.array([1, 2], np.int64), 16, stream=0)
 
 
+def test_build_checks_32_byte_key_order_bytewise(bt):
+    """32-byte keys are ordered by their bytes from the first on: 0x01 0x00..
+    sorts after 0x00 0xff.. although its last byte is smaller."""
+    a = np.zeros((2, 32), np.uint8)
+    a[0, 0], a[0, 31] = 1, 0
+    a[1, 0], a[1, 31] = 0, 255
+    v = np.arange(2, dtype=np.uint64)
+    with pytest.raises(bt.BTreeError) as e:
+        bt.bt_build(a, v, 16, stream=0)
+    assert e.value.code == "BT_ERR_UNSORTED"
+    with pytest.raises(bt.BTreeError) as e:
+        bt.bt_build(np.stack([a[1], a[1]]), v, 16, stream=0)
+    assert e.value.code == "BT_ERR_DUPLICATE"
+    h = bt.bt_build(np.zeros((0, 32), np.uint8), np.zeros(0, np.uint64), 16, stream=0)
+    info = bt.bt_tree_info(h)
+    assert info.key_bytes == 32 and info.height == 0 and info.device_bytes == 0
+    bt.bt_free(h)
+    with pytest.raises(ValueError):
+        bt.bt_build(np.zeros((3, 16), np.uint8), np.zeros(3, np.uint64), 16, stream=0)
+
+
 def test_empty_tree_needs_no_device_memory(bt):
     h = bt.bt_build(np.empty(0, np.uint64), np.empty(0, np.uint64), 32, stream=0)
     info = bt.bt_tree_info(h)

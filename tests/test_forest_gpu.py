@@ -127,7 +127,7 @@ def test_bulk_staging_every_block_size(bt, fanout, key_bits):
     vals = W.rank_values(keys.size, 32)
     tree = bt.BTree(keys, vals, fanout)
     bt.bt_tree_set_staging(tree.handle, bt.BT_STAGE_BULK)
-    o = OracleTree(keys, vals, fanout)
+    o = OracleTree(keys, vals, fanout, val_bits=32)
     q = W.make_queries(keys, 40_003, 0.7, seed=69, width_bits=key_bits)
     for sb in (-1, 0):
         v, f = tree.search(torch.from_numpy(q).cuda(), sort_bits=sb)
