@@ -62,6 +62,7 @@ def parse_args(argv=None):
     p.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain leg")
     p.add_argument("--no-batching", action="store_true", help="skip the multi-tree batching leg")
     p.add_argument("--no-serving", action="store_true", help="skip the serving leg")
+    p.add_argument("--no-paper-keys", action="store_true", help="skip the 32-byte-key leg")
     return p.parse_args(argv)
 
 
@@ -372,6 +373,79 @@ def _learned_case(bt, flush, stream, keys, label):
     bt.bt_model_free(pl)
     bt.bt_model_free(mlp)
     tree.close()
+    return res
+
+
+# ------------------------------------------------------ paper key format leg
+
+def paper_keys_leg(a, bt, flush, stream, peak):
+    """The paper's own tree and key format (Sec. V): 2^20 entries of 32-byte
+    keys (lexicographic byte order) with 8-byte data, fanout 16; batches of
+    1000 queries (the paper's batch size) and 2^20, uniform over the keys,
+    90% hits.  Lookups/s through bt_search_batch, the descent's achieved
+    bandwidth against its algorithmic bytes, a check of every result against
+    numpy's binary search over the keys (byte order), and the byte-key
+    oracle on the host cores as this workload's CPU baseline."""
+    import torch
+    n, m = 1 << 20, 16
+    keys = W.byte_keys(n, 32, seed=W.SEED_BASE + 8)
+    vals = W.rank_values(n, 64)
+    kv = keys.view("V32").ravel()
+    tree = bt.BTree(keys, vals, m)
+    res = {"workload": f"{n} distinct 32-byte keys (uniform random bytes), 8-byte values, fanout {m}, "
+                       "90% hits, uniform queries"}
+    # the largest key under every node, as a key rank, per level (even bulk load)
+    node_max_rank = [x.astype(np.int64) for x in level_node_max(np.arange(n, dtype=np.uint64), tree.level_nodes)]
+    for B, steps in ((1000, 300), (1 << 20, 50)):
+        qh = W.make_byte_queries(keys, B, 0.9, seed=W.SEED_BASE + 9 + B)
+        q = torch.from_numpy(qh).cuda()
+        nb = tree.workspace_bytes(B)
+        ws = torch.empty(max(nb, 1), dtype=torch.uint8, device="cuda")
+        v, f = tree.alloc_outputs(B)
+        fn = lambda: bt.bt_search_batch(tree.handle, q, B, v, f, ws, nb, stream)
+        for _ in range(3):
+            fn()
+        us = _time_calls(fn, steps, flush if B > 4096 else None, stream)
+        rank = np.searchsorted(kv, qh.view("V32").ravel())
+        hit = rank < n
+        hit[hit] = kv[rank[hit]] == qh.view("V32").ravel()[hit]
+        want_v = np.full(B, np.uint64(2**64 - 1))
+        want_v[hit] = vals[rank[hit]]
+        row = {"lookups_per_s": B / (statistics.fmean(us) / 1e6), "p50_us": us[len(us) // 2],
+               "p99_us": us[min(len(us) - 1, int(0.99 * len(us)))],
+               "correct": bool(np.array_equal(v.cpu().numpy(), want_v) and
+                               np.array_equal(f.cpu().numpy(), hit.astype(np.uint8)))}
+        if B > 4096:
+            # the descent alone on the partitioned batch, against its algorithmic bytes
+            sq = torch.empty_like(q)
+            si = torch.empty(B, dtype=torch.int32, device="cuda")
+            bt.bt_sort_batch(tree.handle, q, B, -1, sq, si, ws, nb, stream)
+            dfn = lambda: bt.bt_descend_sorted(tree.handle, sq, si, B, v, f, None, stream)
+            dus = _time_calls(dfn, steps, flush, stream)
+            counts = [int(np.unique(np.minimum(np.searchsorted(mr, rank), mr.size - 1)).size)
+                      for mr in node_max_rank]
+            leaf = np.minimum(np.searchsorted(node_max_rank[-1], rank), node_max_rank[-1].size - 1)
+            first = np.concatenate([[0], node_max_rank[-1][:-1] + 1])
+            slot = rank - first[leaf]
+            sect = np.unique(((leaf[hit] * m + slot[hit]) * 8) // 32).size
+            alg = descend_algorithmic_bytes(counts, int(sect), m, 32, 8, B)
+            d_mean = statistics.fmean(dus)
+            row["descend_us"] = d_mean
+            row["roofline"] = {"bound": "hbm", "achieved": alg / (d_mean / 1e6) / 1e9, "peak": peak,
+                               "unit": "GB/s", "frac": alg / (d_mean / 1e6) / 1e9 / peak,
+                               "algorithmic_bytes_per_launch": alg, "distinct_nodes_per_level": counts}
+        res[f"batch_{B}"] = row
+    tree.close()
+    # CPU baseline for this workload: the byte-key oracle, all host cores
+    from oracle.bytes_keys import OracleBytesTree
+    o = OracleBytesTree(keys, vals, m)
+    sample = W.make_byte_queries(keys, 1 << 18, 0.9, seed=W.SEED_BASE + 10)
+    t0 = time.perf_counter()
+    o.search_mt(sample, os.cpu_count() or 1)
+    dt = time.perf_counter() - t0
+    res["cpu_baseline"] = {"value": sample.shape[0] / dt, "unit": "lookups/s", "cores": os.cpu_count() or 1,
+                           "kind": "oracle", "sample": f"{sample.shape[0]} queries of the same mix"}
+    o.close()
     return res
 
 
@@ -710,6 +784,8 @@ def run_ours(a):
                             "lookups_per_s": b / (statistics.fmean(us) / 1e6)}
         line["small_batch_latency"] = lat
 
+    if not a.no_extras and not a.no_paper_keys:
+        line["paper_keys"] = paper_keys_leg(a, bt, flush, stream, peak)
     if not a.no_extras and not a.no_learned:
         line["learned"] = learned_leg(a, bt, flush, stream)
     if not a.no_extras and not a.no_batching:

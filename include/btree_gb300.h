@@ -149,11 +149,11 @@ uint64_t bt_search_workspace_bytes(const bt_tree *tree, uint64_t nq);
 
 /* Options for bt_search_batch_ex. */
 typedef struct bt_search_opts {
-    /* How many leading bits of the normalised query key the batch is
-     * radix-sorted on before the descent (Sec. IV-A sorts the batch so that
-     * queries for one node are adjacent; see bt_sort_batch for the order
-     * obtained): -1 lets the library choose from nq and the tree, 0 skips
-     * the sort, 1..64 forces that many bits (capped at the key range). */
+    /* Bits of the bucket number the batch is partitioned on before the
+     * descent (Sec. IV-A sorts the batch so that queries for one node are
+     * adjacent; see bt_sort_batch for the order obtained): -1 lets the
+     * library choose from nq (none below 16384 queries), 0 skips the
+     * partition, 1..16 forces that many bits (larger values mean 16). */
     int32_t sort_bits;
     /* If non-NULL: device array of `height` counters to which the search
      * adds, per level, how many node key blocks it fetched -- the quantity
@@ -192,20 +192,20 @@ bt_status bt_search_batch_ex(const bt_tree *tree, const void *d_queries, uint64_
                              bt_stream stream);
 
 /*
- * bt_sort_batch -- the first step of a search on its own: the on-device radix
- * sort of the batch (Sec. IV-A: queries are sorted so that those routed to
- * one node are adjacent).  Writes the reordered queries and, for each, its
- * input position.  The sort key is the query's offset above the tree's
- * smallest key, clamped to the tree's key range (a monotone map, so the
- * order agrees with the key order), of which `sort_bits` leading bits are
- * used (-1 = library choice, 0 = no reordering: the queries are copied and
- * the index is the identity).  Two stages: a distribution of the batch on
- * the leading D = min(sort_bits, 12, ceil(log2(nq / 4096))) bits, then a
- * sort of every aligned run of 4096 positions on all `sort_bits` bits.  The
- * result is ordered on the leading D bits across the batch and on the
- * leading `sort_bits` bits within each aligned run of 4096 positions (for
- * nq <= 4096: a sort on `sort_bits` bits).  The order of queries with equal
- * sort keys is unspecified.
+ * bt_sort_batch -- the first step of a search on its own: the on-device
+ * partition of the batch (Sec. IV-A: queries are sorted so that those
+ * routed to one node are adjacent).  Writes the reordered queries and, for
+ * each, its input position.  The order is that of a bucket number monotone
+ * in the key, on `sort_bits` bits (-1 = library choice: about nq/16
+ * buckets, at most 2^16; 0 = no reordering: the queries are copied and the
+ * index is the identity):
+ *   bucket(q) = (c << r) | s, where c = the number of the tree's splitters
+ *   (bt_info.nsplit keys, see bt_build) smaller than q and s = floor(2^r *
+ *   (q - lo) / (hi - lo + 1)) in fp32 over the splitter segment (lo, hi]
+ *   holding q, clamped to [0, 2^r - 1]; r = sort_bits - bitlen(nsplit)
+ *   when positive, else bucket = c >> (bitlen(nsplit) - sort_bits).
+ * The order of queries with equal buckets is unspecified (it follows the
+ * order of device atomics and may differ between calls).
  *
  *   d_queries         nq keys (device).
  *   d_sorted_queries  nq keys (device), must not overlap d_queries.
@@ -218,8 +218,10 @@ bt_status bt_sort_batch(const bt_tree *tree, const void *d_queries, uint64_t nq,
                         void *d_sorted_queries, uint32_t *d_sorted_index, void *d_workspace,
                         uint64_t ws_bytes, bt_stream stream);
 
-/* Number of kernels the sort of bt_sort_batch / bt_search_batch launches
- * for this tree, batch size and sort_bits (0 = no sort).  -1 on a NULL tree. */
+/* Number of kernels the partition of bt_sort_batch / bt_search_batch
+ * launches for this tree, batch size and sort_bits (0 = no partition; it
+ * also issues one cudaMemsetAsync of its bucket counters).  -1 on a NULL
+ * tree. */
 int32_t bt_sort_launches(const bt_tree *tree, uint64_t nq, int32_t sort_bits);
 
 /*
@@ -371,6 +373,45 @@ bt_status bt_check_timeouts(void);
  */
 bt_status bt_autotune(const void *h_keys, const void *h_vals, uint64_t n, bt_width key_w, bt_width val_w,
                       const void *d_sample, uint64_t nsample, bt_stream stream, bt_tree **out, bt_tune *best);
+
+/* ------------------------------------------------------------------------
+ * The paper's node layout (Sec. IV-B, Eq. 1, Fig. 3), for comparison with
+ * the structure-of-arrays layout above.  The same tree as one array of
+ * equal-size nodes in BFS order (root first, then level by level, left to
+ * right).  A node is:
+ *   a 32-byte header: uint32 slotUse (keys in a leaf, separators in an
+ *     inner node), uint32 depth (level, root = 0), 24 zero bytes;
+ *   k_max = m - 1 key slots in the device key form (unused slots all-ones),
+ *     padded to a multiple of 8 bytes;
+ *   inner nodes: m 8-byte child addresses, byte offsets from the start of
+ *     the array (slots beyond slotUse + 1 are zero);
+ *   leaves: k_max 8-byte data slots (the value, zero-extended) and 8 unused
+ *     bytes;
+ *   rounded up to whole 32-byte chunks (the paper's memory access unit).
+ * For 32-byte keys this is Eq. 1's N_size = 32 + 32 k_max + 32 (k_max+1)/4
+ * = 40 m bytes.
+ * ------------------------------------------------------------------------ */
+
+/* Node size of the paper layout for fanout m and key width (0 if either is
+ * unsupported).  Pure function, no device. */
+uint32_t bt_paper_node_bytes(uint32_t fanout, bt_width key_w);
+
+/* Build the paper layout of `tree` in a second device allocation (freed by
+ * bt_free); copies the tree image to the host and back, synchronizes
+ * `stream`.  A no-op if already built or if the tree is empty.
+ * Errors: BT_ERR_ARG, BT_ERR_NOMEM, BT_ERR_CUDA. */
+bt_status bt_paper_layout_build(bt_tree *tree, bt_stream stream);
+
+/* bt_search_batch over the paper layout: the same partition, then the
+ * level-wise descent over whole staged nodes, following child addresses
+ * (results identical to bt_search_batch).  BT_ERR_ARG if the layout has not
+ * been built.  Other errors as bt_search_batch. */
+bt_status bt_paper_search_batch(const bt_tree *tree, const void *d_queries, uint64_t nq, void *d_out_vals,
+                                uint8_t *d_out_found, void *d_workspace, uint64_t ws_bytes, bt_stream stream);
+
+/* bt_descend_sorted over the paper layout. */
+bt_status bt_paper_descend_sorted(const bt_tree *tree, const void *d_queries, const uint32_t *d_index, uint64_t nq,
+                                  void *d_out_vals, uint8_t *d_out_found, bt_stream stream);
 
 /* ------------------------------------------------------------------------
  * Serving: continuous batching of small lookup requests.  The paper times a

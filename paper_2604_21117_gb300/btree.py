@@ -38,7 +38,8 @@ EXPORTED = ("bt_build", "bt_free", "bt_tree_info", "bt_tree_copy_image", "bt_sea
             "bt_learned_descend_sorted", "bt_learned_search_batch", "bt_model_copy_err_bounds",
             "bt_forest_create", "bt_forest_free",
             "bt_forest_workspace_bytes", "bt_forest_search", "bt_tree_set_launch", "bt_tree_set_staging",
-            "bt_check_timeouts", "bt_autotune",
+            "bt_check_timeouts", "bt_autotune", "bt_paper_node_bytes", "bt_paper_layout_build",
+            "bt_paper_search_batch", "bt_paper_descend_sorted",
             "bt_server_create", "bt_server_submit", "bt_server_poll", "bt_server_drain", "bt_server_get_stats",
             "bt_server_destroy", "bt_server_run_trace")
 
@@ -412,6 +413,38 @@ def bt_autotune(h_keys: np.ndarray, h_vals: np.ndarray, d_sample, nsample: int, 
                           nsample, _stream_handle(stream), ctypes.byref(out), ctypes.byref(best))
     _check("bt_autotune", st)
     return out.value, best
+
+
+_lib.bt_paper_node_bytes.restype = ctypes.c_uint32
+_lib.bt_paper_node_bytes.argtypes = [ctypes.c_uint32, _i]
+_lib.bt_paper_layout_build.restype = _i
+_lib.bt_paper_layout_build.argtypes = [_vp, _vp]
+_lib.bt_paper_search_batch.restype = _i
+_lib.bt_paper_search_batch.argtypes = [_vp, _vp, _u64, _vp, _vp, _vp, _u64, _vp]
+_lib.bt_paper_descend_sorted.restype = _i
+_lib.bt_paper_descend_sorted.argtypes = [_vp, _vp, _vp, _u64, _vp, _vp, _vp]
+
+
+def bt_paper_node_bytes(fanout: int, key_width: int) -> int:
+    """Node size of the paper's layout (Eq. 1); 0 if unsupported."""
+    return int(_lib.bt_paper_node_bytes(fanout, key_width))
+
+
+def bt_paper_layout_build(tree: int, stream=None) -> None:
+    _check("bt_paper_layout_build", _lib.bt_paper_layout_build(tree, _stream_handle(stream)))
+
+
+def bt_paper_search_batch(tree: int, d_queries, nq: int, d_out_vals, d_out_found, d_workspace, ws_bytes: int,
+                          stream=None) -> None:
+    st = _lib.bt_paper_search_batch(tree, _dptr(d_queries), nq, _dptr(d_out_vals), _dptr(d_out_found),
+                                    _dptr(d_workspace), ws_bytes, _stream_handle(stream))
+    _check("bt_paper_search_batch", st)
+
+
+def bt_paper_descend_sorted(tree: int, d_queries, d_index, nq: int, d_out_vals, d_out_found, stream=None) -> None:
+    st = _lib.bt_paper_descend_sorted(tree, _dptr(d_queries), _dptr(d_index), nq, _dptr(d_out_vals),
+                                      _dptr(d_out_found), _stream_handle(stream))
+    _check("bt_paper_descend_sorted", st)
 
 
 class bt_server_opts(ctypes.Structure):

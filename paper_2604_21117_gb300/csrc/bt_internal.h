@@ -44,6 +44,23 @@ struct DevTree {
     uint32_t nsplit;
 };
 
+// The same tree in the paper's node layout (Eq. 1, Fig. 3): one array of
+// equal-size nodes in BFS order (root first, level by level, left to
+// right).  A node: a 32-byte header (uint32 slotUse = keys or separators in
+// use, uint32 depth = level), then k_max = m - 1 key slots (device key form,
+// unused slots all-ones) padded to 8 bytes, then for inner nodes m 8-byte
+// child addresses (byte offsets from the array's start) and for leaves
+// k_max 8-byte data slots (the value, zero-extended) plus 8 unused bytes;
+// the node size is rounded up to whole 32-byte chunks (Sec. IV-B).
+struct PaperTree {
+    const unsigned char *base;
+    uint32_t node_bytes;
+    uint32_t child_off;   // byte offset of the child addresses / data slots in a node
+    int height;
+    int pin_levels;       // top levels copied to shared memory by the descent
+    uint32_t pin_bytes;   // bytes of those levels (a prefix of the array)
+};
+
 // Whole top levels (never the leaves) whose bytes fit `budget`, root first.
 void set_pin_levels(DevTree &d, const bt_info &info, uint32_t budget);
 
@@ -53,6 +70,8 @@ struct bt_tree {
     btgb::DevTree dev;
     bt_info info;
     void *d_image;
+    btgb::PaperTree paper;  // valid once d_paper is set (bt_paper_layout_build)
+    void *d_paper;
 };
 
 struct bt_model {

@@ -334,7 +334,89 @@ extern "C" void bt_free(bt_tree *t)
 {
     if (!t) return;
     if (t->d_image) cudaFree(t->d_image);
+    if (t->d_paper) cudaFree(t->d_paper);
     delete t;
+}
+
+extern "C" uint32_t bt_paper_node_bytes(uint32_t fanout, bt_width key_w)
+{
+    const uint64_t w = static_cast<uint64_t>(key_w), m = fanout;
+    if ((w != 4 && w != 8 && w != 32) || m < 3 || m > 64) return 0;
+    const uint64_t keys = align_up(w * (m - 1), 8);
+    return static_cast<uint32_t>(align_up(32 + keys + 8 * m, 32));
+}
+
+extern "C" bt_status bt_paper_layout_build(bt_tree *t, bt_stream stream)
+{
+    if (!t) return BT_ERR_ARG;
+    if (t->d_paper || t->dev.height == 0) return BT_OK;
+    const DevTree &d = t->dev;
+    const int h = d.height, kb = d.key_bytes, vb = d.val_bytes;
+    const uint64_t m = static_cast<uint64_t>(d.m);
+    const uint32_t nb = bt_paper_node_bytes(static_cast<uint32_t>(m), static_cast<bt_width>(kb));
+    const uint64_t child_off = 32 + align_up(static_cast<uint64_t>(kb) * (m - 1), 8);
+    uint64_t first[BT_MAX_LEVELS + 1];
+    first[0] = 0;
+    for (int l = 0; l < h; ++l) first[l + 1] = first[l] + d.nodes[l];
+    const uint64_t bytes = first[h] * nb;
+    std::vector<unsigned char> soa(t->info.device_bytes);
+    cudaError_t e = cudaMemcpy(soa.data(), t->d_image, soa.size(), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        set_error_detail("copy of tree image to host", e);
+        return BT_ERR_CUDA;
+    }
+    unsigned char *img = static_cast<unsigned char *>(calloc(bytes, 1));
+    if (!img) return BT_ERR_NOMEM;
+    for (int l = 0; l < h; ++l) {
+        const bool leaf = (l + 1 == h);
+        const unsigned char *lk = soa.data() + t->info.level_key_offset[l];
+        for (uint64_t i = 0; i < d.nodes[l]; ++i) {
+            unsigned char *node = img + (first[l] + i) * nb;
+            const uint64_t span = d.cbase[l] + (i < d.crem[l] ? 1 : 0);  // children, or keys of a leaf
+            const uint32_t use = static_cast<uint32_t>(leaf ? span : span - 1);
+            const uint32_t depth = static_cast<uint32_t>(l);
+            memcpy(node, &use, 4);
+            memcpy(node + 4, &depth, 4);
+            memcpy(node + 32, lk + i * m * kb, (m - 1) * kb);  // slots beyond `use` are all-ones already
+            uint64_t *slots = reinterpret_cast<uint64_t *>(node + child_off);
+            if (leaf) {
+                const unsigned char *lv = soa.data() + t->info.leaf_val_offset + i * m * vb;
+                for (uint64_t j = 0; j < span; ++j) slots[j] = load_uint(lv, j, vb);
+            } else {
+                const uint64_t c0 = i * d.cbase[l] + (i < d.crem[l] ? i : d.crem[l]);
+                for (uint64_t j = 0; j < span; ++j) slots[j] = (first[l + 1] + c0 + j) * nb;
+            }
+        }
+    }
+    void *dp = nullptr;
+    e = cudaMalloc(&dp, bytes);
+    if (e != cudaSuccess) {
+        free(img);
+        set_error_detail("cudaMalloc(paper layout)", e);
+        return e == cudaErrorMemoryAllocation ? BT_ERR_NOMEM : BT_ERR_CUDA;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    e = cudaMemcpyAsync(dp, img, bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    free(img);
+    if (e != cudaSuccess) {
+        cudaFree(dp);
+        set_error_detail("copy of paper layout to device", e);
+        return BT_ERR_CUDA;
+    }
+    PaperTree &p = t->paper;
+    p.base = static_cast<const unsigned char *>(dp);
+    p.node_bytes = nb;
+    p.child_off = static_cast<uint32_t>(child_off);
+    p.height = h;
+    p.pin_levels = 0;
+    p.pin_bytes = 0;
+    for (int l = 0; l + 1 < h && first[l + 1] * nb <= 16384; ++l) {
+        p.pin_levels = l + 1;
+        p.pin_bytes = static_cast<uint32_t>(first[l + 1] * nb);
+    }
+    t->d_paper = dp;
+    return BT_OK;
 }
 
 extern "C" bt_status bt_tree_info(const bt_tree *t, bt_info *out)

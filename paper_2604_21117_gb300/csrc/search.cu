@@ -421,6 +421,103 @@ __global__ void __launch_bounds__(kDescWarpsMax * 32) k_descend(
     }
 }
 
+// ---------------------------------------- the paper's node layout (Eq. 1)
+//
+// The same level-wise descent over the array-of-nodes layout of Eq. 1: the
+// warp's distinct nodes (by node ordinal = byte address / node size) are
+// staged whole -- header, keys and child addresses or data -- and each lane
+// follows the child address of its rank, or at a leaf reads the data slot
+// of its rank from the staged node.  Top levels (a prefix of the array) are
+// pinned in shared memory as in k_descend.
+
+template <typename K, int M>
+struct PaperGeom {
+    static constexpr uint32_t keys = (static_cast<uint32_t>((M - 1) * sizeof(K)) + 7u) / 8u * 8u;
+    static constexpr uint32_t bytes = (32u + keys + 8u * M + 31u) / 32u * 32u;
+    static constexpr int slots = bytes >= 2048 ? 2 : (bytes >= 1024 ? 4 : 8);
+};
+
+template <typename K, int M>
+constexpr int paper_smem_per_warp()
+{
+    return PaperGeom<K, M>::slots * static_cast<int>(PaperGeom<K, M>::bytes) + 32 * 4;
+}
+
+template <typename K, typename V, int M>
+__global__ void __launch_bounds__(kDescWarpsMax * 32) k_descend_paper(
+    const PaperTree p, const RawOf<K> *__restrict__ q, const uint32_t *__restrict__ qidx, uint64_t nq,
+    V *__restrict__ out_v, uint8_t *__restrict__ out_f)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    using G = PaperGeom<K, M>;
+    constexpr uint32_t NB = G::bytes;
+    constexpr int SLOTS = G::slots;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    unsigned char *pin = smem;
+    unsigned char *stage = smem + p.pin_bytes + warp * (SLOTS * NB);
+    uint32_t *list = reinterpret_cast<uint32_t *>(smem + p.pin_bytes + nw * (SLOTS * NB)) + warp * 32;
+    for (uint32_t i = threadIdx.x * 16u; i < p.pin_bytes; i += blockDim.x * 16u) cp_async16_ca(pin + i, p.base + i);
+    cp_async_wait_all();
+    __syncthreads();
+
+    const uint64_t nchunks = (nq + 31) / 32;
+    const uint64_t stride = static_cast<uint64_t>(gridDim.x) * nw;
+    const int H = p.height, P = p.pin_levels;
+    for (uint64_t c = static_cast<uint64_t>(blockIdx.x) * nw + warp; c < nchunks; c += stride) {
+        const uint64_t pos = c * 32 + lane;
+        const bool valid = pos < nq;
+        // tail lanes follow lane 0's query so they never add a node fetch
+        const K key = KeyOps<K>::load(q, valid ? pos : c * 32);
+        const uint32_t dst = valid ? (qidx ? qidx[pos] : static_cast<uint32_t>(pos)) : 0u;
+        uint64_t addr = 0;  // the root is the first node
+        int l = 0;
+        for (; l < P; ++l) {
+            const unsigned char *node = pin + addr;
+            const int r = block_rank<K, M>(reinterpret_cast<const K *>(node + 32), key);
+            addr = *reinterpret_cast<const uint64_t *>(node + p.child_off + 8u * r);
+        }
+        for (; l < H; ++l) {
+            const uint32_t ord = static_cast<uint32_t>(addr / NB);
+            int U, slot;
+            warp_distinct(ord, lane, list, U, slot);
+            __syncwarp();
+            uint64_t next = 0;
+            bool hit = false;
+            V val = static_cast<V>(~static_cast<V>(0));
+            for (int rb = 0; rb < U; rb += SLOTS) {
+                const int nu = (U - rb < SLOTS) ? U - rb : SLOTS;
+                constexpr int CH = NB / 16;
+                for (int i = lane; i < nu * CH; i += 32) {
+                    const int u = i / CH, part = i - u * CH;
+                    cp_async16_cg(stage + u * NB + part * 16,
+                                  p.base + static_cast<uint64_t>(list[rb + u]) * NB + part * 16);
+                }
+                cp_async_wait_all();
+                __syncwarp();
+                if (slot >= rb && slot < rb + nu) {
+                    const unsigned char *node = stage + (slot - rb) * NB;
+                    const K *keys = reinterpret_cast<const K *>(node + 32);
+                    const int r = block_rank<K, M>(keys, key);
+                    if (l + 1 < H) {
+                        next = *reinterpret_cast<const uint64_t *>(node + p.child_off + 8u * r);
+                    } else {
+                        const uint32_t use = *reinterpret_cast<const uint32_t *>(node);
+                        hit = (static_cast<uint32_t>(r) < use) && (keys[r] == key);
+                        if (hit) val = static_cast<V>(*reinterpret_cast<const uint64_t *>(node + p.child_off + 8u * r));
+                    }
+                }
+                __syncwarp();
+            }
+            if (l + 1 < H) {
+                addr = next;
+            } else if (valid) {
+                out_v[dst] = val;
+                out_f[dst] = hit ? 1 : 0;
+            }
+        }
+    }
+}
+
 template <typename V>
 __global__ void k_fill_miss(V *__restrict__ out_v, uint8_t *__restrict__ out_f, uint64_t nq)
 {
@@ -569,6 +666,54 @@ static cudaError_t descend(const DevTree &t, const void *q, const uint32_t *qidx
 {
     const DescendArgs a{&t, q, qidx, nq, out_v, out_f, fetch, nullptr, nullptr};
     return descend_any(a, s);
+}
+
+template <typename K, typename V, int M>
+static cudaError_t launch_paper(const PaperTree &p, const void *q, const uint32_t *qidx, uint64_t nq, void *out_v,
+                                uint8_t *out_f, int nw, cudaStream_t s)
+{
+    auto kern = k_descend_paper<K, V, M>;
+    const int smem = static_cast<int>(p.pin_bytes) + nw * paper_smem_per_warp<K, M>();
+    static const cudaError_t attr = cudaFuncSetAttribute(
+        kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 + kDescWarpsMax * paper_smem_per_warp<K, M>());
+    if (attr != cudaSuccess) return attr;
+    int b = 0, dev = 0, sms = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, nw * 32, smem);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    uint64_t grid = ((nq + 31) / 32 + nw - 1) / nw;
+    const uint64_t cap = static_cast<uint64_t>(sms) * (b > 0 ? b : 1);
+    if (grid > cap) grid = cap;
+    kern<<<static_cast<unsigned>(grid), nw * 32, smem, s>>>(p, static_cast<const RawOf<K> *>(q), qidx, nq,
+                                                          static_cast<V *>(out_v), out_f);
+    return cudaGetLastError();
+}
+
+template <typename K, typename V>
+static cudaError_t paper_m(const DevTree &t, const PaperTree &p, const void *q, const uint32_t *qidx, uint64_t nq,
+                           void *out_v, uint8_t *out_f, cudaStream_t s)
+{
+    const int nw = t.warps > 0 ? t.warps : kDescWarpsDefault;
+    switch (t.m) {
+    case 8: return launch_paper<K, V, 8>(p, q, qidx, nq, out_v, out_f, nw, s);
+    case 16: return launch_paper<K, V, 16>(p, q, qidx, nq, out_v, out_f, nw, s);
+    case 32: return launch_paper<K, V, 32>(p, q, qidx, nq, out_v, out_f, nw, s);
+    default: return launch_paper<K, V, 64>(p, q, qidx, nq, out_v, out_f, nw, s);
+    }
+}
+
+static cudaError_t descend_paper(const DevTree &t, const PaperTree &p, const void *q, const uint32_t *qidx,
+                                 uint64_t nq, void *out_v, uint8_t *out_f, cudaStream_t s)
+{
+    if (t.key_bytes == 32)
+        return t.val_bytes == 8 ? paper_m<Key32, uint64_t>(t, p, q, qidx, nq, out_v, out_f, s)
+                                : paper_m<Key32, uint32_t>(t, p, q, qidx, nq, out_v, out_f, s);
+    if (t.key_bytes == 8)
+        return t.val_bytes == 8 ? paper_m<uint64_t, uint64_t>(t, p, q, qidx, nq, out_v, out_f, s)
+                                : paper_m<uint64_t, uint32_t>(t, p, q, qidx, nq, out_v, out_f, s);
+    return t.val_bytes == 8 ? paper_m<uint32_t, uint64_t>(t, p, q, qidx, nq, out_v, out_f, s)
+                            : paper_m<uint32_t, uint32_t>(t, p, q, qidx, nq, out_v, out_f, s);
 }
 
 template <typename K>
@@ -937,4 +1082,64 @@ extern "C" bt_status bt_check_timeouts(void)
         return BT_ERR_CUDA;
     }
     return v ? BT_ERR_TIMEOUT : BT_OK;
+}
+
+extern "C" bt_status bt_paper_descend_sorted(const bt_tree *tree, const void *d_queries, const uint32_t *d_index,
+                                             uint64_t nq, void *d_out_vals, uint8_t *d_out_found, bt_stream stream)
+{
+    if (!tree) return BT_ERR_ARG;
+    if (nq == 0) return BT_OK;
+    if (nq >= (1ull << 31)) return BT_ERR_ARG;
+    if (!d_queries || !d_out_vals || !d_out_found) return BT_ERR_ARG;
+    if (tree->dev.height > 0 && !tree->d_paper) return BT_ERR_ARG;
+    if (tree->dev.height == 0) return bt_descend_sorted(tree, d_queries, d_index, nq, d_out_vals, d_out_found,
+                                                        nullptr, stream);
+    const cudaError_t e = descend_paper(tree->dev, tree->paper, d_queries, d_index, nq, d_out_vals, d_out_found,
+                                        reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) {
+        set_error_detail("paper-layout descent launch", e);
+        return BT_ERR_CUDA;
+    }
+    return BT_OK;
+}
+
+extern "C" bt_status bt_paper_search_batch(const bt_tree *tree, const void *d_queries, uint64_t nq, void *d_out_vals,
+                                           uint8_t *d_out_found, void *d_workspace, uint64_t ws_bytes,
+                                           bt_stream stream)
+{
+    if (!tree) return BT_ERR_ARG;
+    if (nq == 0) return BT_OK;
+    if (nq >= (1ull << 31)) return BT_ERR_ARG;
+    if (!d_queries || !d_out_vals || !d_out_found) return BT_ERR_ARG;
+    const DevTree &t = tree->dev;
+    if (t.height > 0 && !tree->d_paper) return BT_ERR_ARG;
+    if (t.height == 0)
+        return bt_search_batch(tree, d_queries, nq, d_out_vals, d_out_found, d_workspace, ws_bytes, stream);
+    const WsLayout w = ws_layout(t.key_bytes, nq);
+    if (!d_workspace || ws_bytes < w.total || (reinterpret_cast<uintptr_t>(d_workspace) & 255u))
+        return BT_ERR_WORKSPACE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const PartPlan pp = plan_partition(t, -1, nq);
+    const void *q = d_queries;
+    const uint32_t *qidx = nullptr;
+    unsigned char *ws = static_cast<unsigned char *>(d_workspace);
+    cudaError_t e;
+    if (pp.bits > 0) {
+        void *dq;
+        uint32_t *di;
+        internal_sort_dst(ws, w, &dq, &di);
+        e = sort_any(t, d_queries, nq, pp, ws, w, dq, di, s);
+        if (e != cudaSuccess) {
+            set_error_detail("batch partition launch", e);
+            return BT_ERR_CUDA;
+        }
+        q = dq;
+        qidx = di;
+    }
+    e = descend_paper(t, tree->paper, q, qidx, nq, d_out_vals, d_out_found, s);
+    if (e != cudaSuccess) {
+        set_error_detail("paper-layout descent launch", e);
+        return BT_ERR_CUDA;
+    }
+    return BT_OK;
 }

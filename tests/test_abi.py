@@ -124,3 +124,27 @@ def test_server_and_forest_argument_checks(bt):
     assert lib.bt_forest_create(None, 0, ctypes.byref(out)) == 1
     assert lib.bt_forest_workspace_bytes(9) == 40
     assert lib.bt_tree_set_launch(None, 8, 0) == 1
+
+
+def test_paper_node_bytes_follows_eq1(bt):
+    """Eq. 1: N_size = 32 + 32 k_max + 32 (k_max + 1) / 4 = 40 m bytes for
+    32-byte keys; integer keys keep the 32-byte header and 8-byte child
+    addresses, padded to whole 32-byte chunks."""
+    for m in (8, 16, 32, 64):
+        kmax = m - 1
+        assert bt.bt_paper_node_bytes(m, bt.BT_B32) == 32 + 32 * kmax + 32 * (kmax + 1) // 4 == 40 * m
+        for w in (4, 8):
+            raw = 32 + -(-(w * kmax) // 8) * 8 + 8 * m
+            got = bt.bt_paper_node_bytes(m, w)
+            assert got % 32 == 0 and raw <= got < raw + 32
+    assert bt.bt_paper_node_bytes(2, bt.BT_U64) == 0 and bt.bt_paper_node_bytes(16, 16) == 0
+
+
+def test_paper_layout_entry_points_check_arguments(bt):
+    h = bt.bt_build(np.empty(0, np.uint64), np.empty(0, np.uint64), 16, stream=0)
+    bt.bt_paper_layout_build(h, stream=0)  # empty tree: nothing to build
+    with pytest.raises(bt.BTreeError) as e:
+        bt.bt_paper_search_batch(0, 256, 10, 512, 768, 1024, 1 << 20, stream=0)
+    assert e.value.code == "BT_ERR_ARG"
+    bt.bt_paper_search_batch(h, 0, 0, 0, 0, 0, 0, stream=0)  # nq = 0 is a no-op
+    bt.bt_free(h)

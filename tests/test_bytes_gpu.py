@@ -66,7 +66,7 @@ def test_parity_every_fanout_and_value_width(bt, m, vbits):
 def test_shared_prefixes(bt, prefix):
     """Keys that share their first `prefix` bytes: the partition interpolates
     on the bytes after the shared ones."""
-    keys = W.byte_keys(100_000 if prefix < 30 else 20_000, 32, seed=910 + prefix, prefix_bytes=prefix)
+    keys = W.byte_keys(100_000 if prefix < 30 else 10_000, 32, seed=910 + prefix, prefix_bytes=prefix)
     vals = W.rank_values(keys.shape[0], 64)
     tree = bt.BTree(keys, vals, 16)
     o = OracleBytesTree(keys, vals, 16)

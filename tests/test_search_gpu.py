@@ -275,7 +275,8 @@ def _check_sort_contract(bt, tree, keys, q, hsq, hsi, sb):
     for s0, e0 in zip(starts, ends):
         seg = int(c[s0])
         bw = (int(hi[seg]) - int(lo[seg]) + 1) / (1 << r)
-        run = k[s0:e0].astype(np.float64)
+        # keys beyond the key range share the end buckets
+        run = np.clip(k[s0:e0], np.uint64(keys[0]), np.uint64(keys[-1])).astype(np.float64)
         back = np.maximum.accumulate(run) - run
         assert back.max() <= bw * 1.01 + 2, (seg, back.max(), bw)
 
