@@ -54,6 +54,9 @@ def parse_args(argv=None):
     p.add_argument("--hit", type=float, default=0.9)
     p.add_argument("--zipf", type=float, default=None)
     p.add_argument("--sort-bits", type=int, default=-1)
+    p.add_argument("--l2", choices=["write", "read", "none"], default="write",
+                   help="between timed steps: overwrite a 256 MB buffer (default), read one, or nothing "
+                        "(the 282 MB tree already exceeds L2)")
     p.add_argument("--staging", type=int, default=0, help="node staging: 0 = 16-byte cp.async, 1 = bulk copy")
     p.add_argument("--warps", type=int, default=0, help="descent warps per block (0 = library default)")
     p.add_argument("--pin", type=int, default=-1, help="pinned top-level bytes (-1 = library default)")
@@ -434,6 +437,26 @@ def paper_keys_leg(a, bt, flush, stream, peak):
             row["roofline"] = {"bound": "hbm", "achieved": alg / (d_mean / 1e6) / 1e9, "peak": peak,
                                "unit": "GB/s", "frac": alg / (d_mean / 1e6) / 1e9 / peak,
                                "algorithmic_bytes_per_launch": alg, "distinct_nodes_per_level": counts}
+        # the same search over the paper's node layout (Eq. 1: whole nodes of 40 m bytes)
+        bt.bt_paper_layout_build(tree.handle)
+        pfn = lambda: bt.bt_paper_search_batch(tree.handle, q, B, v, f, ws, nb, stream)
+        for _ in range(3):
+            pfn()
+        pus = _time_calls(pfn, steps, flush if B > 4096 else None, stream)
+        prow = {"lookups_per_s": B / (statistics.fmean(pus) / 1e6), "p50_us": pus[len(pus) // 2],
+                "correct": bool(np.array_equal(v.cpu().numpy(), want_v) and
+                                np.array_equal(f.cpu().numpy(), hit.astype(np.uint8)))}
+        if B > 4096:
+            pdfn = lambda: bt.bt_paper_descend_sorted(tree.handle, sq, si, B, v, f, stream)
+            pdus = _time_calls(pdfn, steps, flush, stream)
+            nbytes = bt.bt_paper_node_bytes(m, bt.BT_B32)
+            palg = sum(counts) * nbytes + B * (32 + 4) + B * (8 + 1)
+            pd = statistics.fmean(pdus)
+            prow["descend_us"] = pd
+            prow["roofline"] = {"bound": "hbm", "achieved": palg / (pd / 1e6) / 1e9, "peak": peak, "unit": "GB/s",
+                                "frac": palg / (pd / 1e6) / 1e9 / peak, "algorithmic_bytes_per_launch": palg,
+                                "node_bytes": nbytes}
+        row["paper_layout"] = prow
         res[f"batch_{B}"] = row
     tree.close()
     # CPU baseline for this workload: the byte-key oracle, all host cores
@@ -648,8 +671,16 @@ def run_ours(a):
     nb = tree.workspace_bytes(B)
     ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    flush.fill_(0)
+    flush_sink = torch.empty(1, dtype=torch.int64, device="cuda")
     stream = torch.cuda.current_stream()
     sort_bits = a.sort_bits
+
+    def clear_l2(i):
+        if a.l2 == "write":
+            flush.fill_(i)
+        elif a.l2 == "read":  # leaves clean lines: no write-back inside the step
+            torch.sum(flush, dtype=torch.int64, out=flush_sink)
 
     def step(i):
         x = dq[i % pool]
@@ -659,7 +690,7 @@ def run_ours(a):
     sampler = ClockSampler(local)
     sampler.start()
     for i in range(a.warmup):
-        flush.fill_(i)
+        clear_l2(i)
         step(i)
     torch.cuda.synchronize()
 
@@ -669,7 +700,7 @@ def run_ours(a):
     torch.cuda.synchronize()
     t_wall0 = time.perf_counter()
     for i in range(K):
-        flush.fill_(i)
+        clear_l2(i)
         e0, e1, e2 = ev[i]
         x = dq[i % pool]
         e0.record(stream)
@@ -719,7 +750,9 @@ def run_ours(a):
                    "hit_frac": a.hit, "query_dist": "uniform" if a.zipf is None else f"zipf{a.zipf}",
                    "sort_bits": "auto" if sort_bits < 0 else sort_bits,
                    "staging": "bulk" if a.staging == 1 else "cp.async",
-                   "l2": "flushed before every timed step (256 MB device write)",
+                   "l2": {"write": "flushed before every timed step (256 MB device write)",
+                          "read": "flushed before every timed step (256 MB device read)",
+                          "none": "not flushed: the 282 MB tree exceeds the 129 MB L2"}[a.l2],
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "p50_us": 1e3 * sdev[len(sdev) // 2], "p99_us": 1e3 * sdev[min(len(sdev) - 1, int(0.99 * len(sdev)))],
         "iqm_us": 1e3 * iqm(step_ms),
@@ -748,7 +781,7 @@ def run_ours(a):
         Ke = max(10, min(K, 200))
         tt = []
         for i in range(Ke):
-            flush.fill_(i)
+            clear_l2(i)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)

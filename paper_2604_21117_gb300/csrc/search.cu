@@ -175,6 +175,39 @@ __device__ __forceinline__ uint32_t child_of(const DevTree &t, int l, uint32_t n
     return node * base + (node < rem ? node : rem) + static_cast<uint32_t>(r);
 }
 
+// Stage nu node blocks of CH 16-byte chunks (block i of `src` array at
+// list[i]) into consecutive shared-memory slots with 16-byte asynchronous
+// copies: CH lanes per block when CH <= 32 (32 / CH blocks per round, no
+// divisions), else the warp walks each block.  `.cg` (L2 only) for leaves,
+// `.ca` for inner levels.
+template <int CH>
+__device__ __forceinline__ void stage_blocks(unsigned char *dst, const unsigned char *src, uint32_t blk_bytes,
+                                             const uint32_t *list, int nu, int lane, bool leaf)
+{
+    if constexpr (CH <= 32) {
+        constexpr int NPI = 32 / CH;
+        const int part = lane % CH;
+        for (int u = lane / CH; u < nu; u += NPI) {
+            const unsigned char *s = src + static_cast<uint64_t>(list[u]) * blk_bytes + part * 16;
+            unsigned char *d = dst + u * blk_bytes + part * 16;
+            if (leaf)
+                cp_async16_cg(d, s);
+            else
+                cp_async16_ca(d, s);
+        }
+    } else {
+        for (int u = 0; u < nu; ++u)
+            for (int part = lane; part < CH; part += 32) {
+                const unsigned char *s = src + static_cast<uint64_t>(list[u]) * blk_bytes + part * 16;
+                unsigned char *d = dst + u * blk_bytes + part * 16;
+                if (leaf)
+                    cp_async16_cg(d, s);
+                else
+                    cp_async16_ca(d, s);
+            }
+    }
+}
+
 // Leaf-max entries a warp can stage for its model windows.
 constexpr int kLeafMaxCap = 128;
 // PL models with at most this many segments are copied to shared memory.
@@ -375,16 +408,8 @@ __global__ void __launch_bounds__(kDescWarpsMax * 32) k_descend(
                     }
                     phase ^= 1u;
                 } else {
-                    for (int i = lane; i < nu * CH; i += 32) {
-                        const int u = i / CH, part = i - u * CH;
-                        const unsigned char *src = reinterpret_cast<const unsigned char *>(
-                                                       lk + static_cast<uint64_t>(list[rb + u]) * M) + part * 16;
-                        unsigned char *dp = reinterpret_cast<unsigned char *>(stage + u * M) + part * 16;
-                        if (last)
-                            cp_async16_cg(dp, src);
-                        else
-                            cp_async16_ca(dp, src);
-                    }
+                    stage_blocks<CH>(reinterpret_cast<unsigned char *>(stage), reinterpret_cast<const unsigned char *>(lk),
+                                     M * static_cast<uint32_t>(sizeof(K)), list + rb, nu, lane, last);
                     cp_async_wait_all();
                 }
                 __syncwarp();
@@ -486,12 +511,7 @@ __global__ void __launch_bounds__(kDescWarpsMax * 32) k_descend_paper(
             V val = static_cast<V>(~static_cast<V>(0));
             for (int rb = 0; rb < U; rb += SLOTS) {
                 const int nu = (U - rb < SLOTS) ? U - rb : SLOTS;
-                constexpr int CH = NB / 16;
-                for (int i = lane; i < nu * CH; i += 32) {
-                    const int u = i / CH, part = i - u * CH;
-                    cp_async16_cg(stage + u * NB + part * 16,
-                                  p.base + static_cast<uint64_t>(list[rb + u]) * NB + part * 16);
-                }
+                stage_blocks<NB / 16>(stage, p.base, NB, list + rb, nu, lane, true);
                 cp_async_wait_all();
                 __syncwarp();
                 if (slot >= rb && slot < rb + nu) {
