@@ -41,6 +41,8 @@ struct DevTree {
     const void *split;
     const float *split_inv;
     const unsigned char *split_off;  // 32-byte keys: bytes shared within each segment
+    const uint16_t *split_R;         // integer keys: splitter pre-index by leading key bits
+    int split_rshift;
     uint32_t nsplit;
 };
 

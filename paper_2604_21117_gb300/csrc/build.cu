@@ -193,7 +193,7 @@ extern "C" bt_status bt_build(const void *h_keys, const void *h_vals, uint64_t n
     }
     t->info.leaf_val_offset = off;
     uint32_t nsplit = 0;
-    uint64_t split_off_offset = 0;
+    uint64_t split_off_offset = 0, split_R_offset = 0;
     if (h > 0) {
         off = align_up(off + up[0] * m * vb, 256);
         nsplit = static_cast<uint32_t>(up[0] - 1 < 1023 ? up[0] - 1 : 1023);
@@ -204,6 +204,9 @@ extern "C" bt_status bt_build(const void *h_keys, const void *h_vals, uint64_t n
         if (kb == 32) {
             split_off_offset = off;
             off = align_up(off + static_cast<uint64_t>(nsplit) + 1, 256);
+        } else {
+            split_R_offset = off;
+            off = align_up(off + ((1ull << 12) + 1) * 2, 256);
         }
     }
     t->info.nsplit = nsplit;
@@ -281,6 +284,19 @@ extern "C" bt_status bt_build(const void *h_keys, const void *h_vals, uint64_t n
             }
             sinv[c] = static_cast<float>(1.0 / (width + 1.0));
         }
+        if (kb != 32) {
+            // pre-index: R[j] = splitters whose leading 12 bits above kmin are < j
+            const uint64_t range = d.kmax - d.kmin;
+            int rl = 0;
+            while (rl < 64 && (range >> rl) != 0) ++rl;
+            d.split_rshift = rl > 12 ? rl - 12 : 0;
+            uint16_t *R = reinterpret_cast<uint16_t *>(img + split_R_offset);
+            uint32_t c = 0;
+            for (uint32_t j = 0; j <= (1u << 12); ++j) {
+                while (c < nsplit && ((load_uint(sk, c, kb) - d.kmin) >> d.split_rshift) < j) ++c;
+                R[j] = static_cast<uint16_t>(c);
+            }
+        }
     }
     // Inner levels bottom-up: separator j = largest key under child j.
     for (int l = leaf - 1; l >= 0; --l) {
@@ -325,6 +341,8 @@ extern "C" bt_status bt_build(const void *h_keys, const void *h_vals, uint64_t n
     d.split = static_cast<unsigned char *>(t->d_image) + t->info.split_offset;
     d.split_inv = reinterpret_cast<const float *>(static_cast<unsigned char *>(t->d_image) + t->info.split_inv_offset);
     d.split_off = kb == 32 ? static_cast<unsigned char *>(t->d_image) + split_off_offset : nullptr;
+    d.split_R = kb == 32 ? nullptr
+                         : reinterpret_cast<const uint16_t *>(static_cast<unsigned char *>(t->d_image) + split_R_offset);
     t->info.d_image = t->d_image;
     *out = t;
     return BT_OK;

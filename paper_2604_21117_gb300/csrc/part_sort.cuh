@@ -18,14 +18,16 @@
 //          interpolate on the 8 bytes that follow the bytes the segment's
 //          bounds (hence all its keys) share.
 //
-//   k_part_count    per query: its bucket; warp-aggregated atomic counts
-//                   (equal buckets within a warp are counted once, so a hot
-//                   key costs one atomic per warp).  The last block to finish
-//                   (a ticket counter, no waiting) turns the counts into
-//                   exclusive bucket starts.
-//   k_part_scatter  per query: a slot in its bucket from a warp-aggregated
-//                   atomic cursor; the query and its input position are
-//                   written there.
+//   k_part_hist     per block, the bucket counts of a slice of the batch in
+//                   shared memory, added to the global totals once per
+//                   non-zero bucket (a hot key costs one global atomic per
+//                   block); the last block to finish (a ticket counter, no
+//                   waiting) turns the totals into exclusive bucket starts.
+//   k_part_scatter  per block and round of queries: shared-memory bucket
+//                   counts, one global atomic per non-zero bucket to
+//                   reserve its run, then each query's slot in the run from
+//                   a shared-memory atomic; the query and its input position
+//                   are written there.
 //
 // Result: the batch ordered by bucket; the order of queries within one
 // bucket is unspecified (it depends on the order of the atomics).
@@ -40,10 +42,10 @@
 namespace btgb {
 
 constexpr int kSplitSlots = 1023;   // splitters per tree, at most
+constexpr int kRadixBits = 12;      // pre-index of the splitters by leading key bits
 constexpr int kSplitBits = 10;      // bits of c with the full table
-constexpr int kMaxPartBits = 16;    // bucket bits, at most (2^16 counters)
+constexpr int kMaxPartBits = 14;    // bucket bits, at most (2^14 counters in shared memory)
 constexpr int kPartThreads = 1024;
-constexpr int kPartUnroll = 4;
 
 // Per-search view of the tree's splitter table.
 template <typename K>
@@ -51,6 +53,8 @@ struct PartNorm {
     const K *split;         // nsplit splitters, ascending (device)
     const float *split_inv; // nsplit + 1 reciprocal segment widths (device)
     const unsigned char *split_off;  // 32-byte keys: per segment, bytes its keys share
+    const uint16_t *split_R;         // integer keys: R[j] = splitters whose leading bits are < j
+    int rshift;                      // leading bits = (key - kmin) >> rshift
     K kmin;                 // smallest key: lower bound of segment 0
     K kmax;                 // largest key: upper bound of the last segment
     uint32_t nsplit;
@@ -66,6 +70,7 @@ struct PartSmem {
     K sp[kSplitSlots + 1];
     float inv[kSplitSlots + 1];
     unsigned char off[kSplitSlots + 1];
+    uint16_t R[(1 << kRadixBits) + 1];
     uint32_t scan_tmp[32];
     uint32_t last;
 };
@@ -78,15 +83,34 @@ __device__ __forceinline__ void part_load_tables(PartSmem<K> &S, const PartNorm<
         S.inv[i] = i <= static_cast<int>(pn.nsplit) ? pn.split_inv[i] : 0.0f;
         S.off[i] = (pn.split_off && i <= static_cast<int>(pn.nsplit)) ? pn.split_off[i] : 0;
     }
+    if (pn.split_R)
+        for (int i = threadIdx.x; i <= (1 << kRadixBits); i += blockDim.x) S.R[i] = pn.split_R[i];
 }
 
 template <typename K>
 __device__ __forceinline__ uint32_t part_bucket(const PartSmem<K> &S, const PartNorm<K> &pn, K q)
 {
-    uint32_t c = 0;
+    uint32_t c;
+    if (pn.split_R) {
+        // the splitters whose leading bits equal q's bracket c; search only those
+        const uint64_t d0 = q > pn.kmin ? static_cast<uint64_t>(q - pn.kmin) : 0ull;
+        const uint64_t j64 = d0 >> pn.rshift;
+        const uint32_t j = j64 < (1u << kRadixBits) ? static_cast<uint32_t>(j64) : (1u << kRadixBits) - 1u;
+        uint32_t lo = S.R[j], hi = S.R[j + 1];
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (S.sp[mid] < q)
+                lo = mid + 1;
+            else
+                hi = mid;
+        }
+        c = lo;
+    } else {
+        c = 0;
 #pragma unroll
-    for (uint32_t h = (kSplitSlots + 1) / 2; h >= 1; h >>= 1)
-        if (S.sp[c + h - 1] < q) c += h;
+        for (uint32_t h = (kSplitSlots + 1) / 2; h >= 1; h >>= 1)
+            if (S.sp[c + h - 1] < q) c += h;
+    }
     if (pn.r == 0) return c >> pn.cshift;
     const K lo = c ? S.sp[c - 1] : pn.kmin;
     const float d = q > lo ? static_cast<float>(static_cast<uint64_t>(q - lo)) : 0.0f;
@@ -153,101 +177,142 @@ __device__ __forceinline__ uint32_t part_block_excl_scan(uint32_t v, uint32_t *t
     return r;
 }
 
-// counts[0..nb) must be zero and counts[nb] (the ticket) zero on entry; on
-// exit counts[b] is the first position of bucket b.  nb is a multiple of 4.
+// Queries a block of k_part_scatter holds (in registers) per round.
 template <typename K>
-__global__ void __launch_bounds__(kPartThreads) k_part_count(const RawOf<K> *__restrict__ q, uint64_t nq, PartNorm<K> pn,
-                                                             uint32_t *__restrict__ counts, uint32_t nb)
+constexpr int part_per_thread()
+{
+    return sizeof(K) > 8 ? 4 : 8;
+}
+
+// Bucket histogram.  Each block counts the buckets of one contiguous slice
+// of the batch in shared memory (dynamic, nb words), then adds its non-zero
+// counts to total[] (nb words, zero on entry).  total[nb] is a ticket (zero
+// on entry): the last block to finish turns total[] into exclusive bucket
+// starts.  nb is a multiple of 4.
+template <typename K>
+__global__ void __launch_bounds__(kPartThreads) k_part_hist(const RawOf<K> *__restrict__ q, uint64_t nq, PartNorm<K> pn,
+                                                            uint32_t *__restrict__ total, uint32_t nb)
 {
     __shared__ PartSmem<K> S;
+    extern __shared__ uint32_t cnt[];
     part_load_tables(S, pn);
+    for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x) cnt[j] = 0;
     __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
-    for (uint64_t i0 = static_cast<uint64_t>(blockIdx.x) * blockDim.x + (threadIdx.x & ~31u); i0 < nq;
-         i0 += stride * kPartUnroll) {
-        RawOf<K> key[kPartUnroll];
+    const uint64_t per = (nq + gridDim.x - 1) / gridDim.x;
+    const uint64_t s0 = blockIdx.x * per, s1 = s0 + per < nq ? s0 + per : nq;
+    constexpr int U = 4;
+    for (uint64_t i0 = s0 + threadIdx.x; i0 < s1; i0 += static_cast<uint64_t>(U) * blockDim.x) {
+        RawOf<K> key[U];
 #pragma unroll
-        for (int u = 0; u < kPartUnroll; ++u) {
-            const uint64_t i = i0 + u * stride + lane;
-            if (i < nq) key[u] = q[i];
+        for (int u = 0; u < U; ++u) {
+            const uint64_t i = i0 + static_cast<uint64_t>(u) * blockDim.x;
+            if (i < s1) key[u] = q[i];
         }
 #pragma unroll
-        for (int u = 0; u < kPartUnroll; ++u) {
-            const uint64_t i = i0 + u * stride + lane;
-            const unsigned vm = __ballot_sync(0xffffffffu, i < nq);
-            if (i < nq) {
-                const uint32_t b = part_bucket(S, pn, KeyOps<K>::from_raw(key[u]));
-                const unsigned same = __match_any_sync(vm, b);
-                if ((same & part_lanemask_lt()) == 0) atomicAdd(counts + b, static_cast<uint32_t>(__popc(same)));
-            }
-        }
+        for (int u = 0; u < U; ++u)
+            if (i0 + static_cast<uint64_t>(u) * blockDim.x < s1)
+                atomicAdd(cnt + part_bucket(S, pn, KeyOps<K>::from_raw(key[u])), 1u);
     }
-    // The last block to get here scans the counts (all other blocks' atomics
+    __syncthreads();
+    for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x)
+        if (cnt[j]) atomicAdd(total + j, cnt[j]);
+    // The last block to get here scans the totals (every other block's adds
     // are visible to it after their fences and its ticket).
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) S.last = (atomicAdd(counts + nb, 1u) == gridDim.x - 1) ? 1u : 0u;
+    if (threadIdx.x == 0) S.last = (atomicAdd(total + nb, 1u) == gridDim.x - 1) ? 1u : 0u;
     __syncthreads();
     if (!S.last) return;
     __threadfence();
-    const uint32_t per = (nb / 4 + blockDim.x - 1) / blockDim.x;  // uint4 groups per thread
-    uint4 *c4 = reinterpret_cast<uint4 *>(counts);
-    const uint32_t g0 = threadIdx.x * per;
+    const uint32_t groups = nb / 4;
+    const uint32_t per4 = (groups + blockDim.x - 1) / blockDim.x;  // uint4 groups per thread
+    uint4 *t4 = reinterpret_cast<uint4 *>(total);
+    const uint32_t g0 = threadIdx.x * per4;
+    uint4 v[4];  // nb <= 2^14 and 1024 threads: at most 4 groups per thread
     uint32_t sum = 0;
-#pragma unroll 4
-    for (uint32_t g = g0; g < g0 + per && g < nb / 4; ++g) {
-        const uint4 v = __ldcg(c4 + g);
-        sum += v.x + v.y + v.z + v.w;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const uint32_t g = g0 + k;
+        v[k] = (k < static_cast<int>(per4) && g < groups) ? __ldcg(t4 + g) : make_uint4(0, 0, 0, 0);
+        sum += v[k].x + v[k].y + v[k].z + v[k].w;
     }
     uint32_t run = part_block_excl_scan(sum, S.scan_tmp);
-    for (uint32_t g = g0; g < g0 + per && g < nb / 4; ++g) {
-        uint4 v = __ldcg(c4 + g);
-        const uint32_t a = run, b = a + v.x, c = b + v.y, d = c + v.z;
-        run = d + v.w;
-        v.x = a;
-        v.y = b;
-        v.z = c;
-        v.w = d;
-        c4[g] = v;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const uint32_t g = g0 + k;
+        if (k < static_cast<int>(per4) && g < groups) {
+            const uint32_t a0 = run, a1 = a0 + v[k].x, a2 = a1 + v[k].y, a3 = a2 + v[k].z;
+            run = a3 + v[k].w;
+            t4[g] = make_uint4(a0, a1, a2, a3);
+        }
     }
 }
 
+// Scatter.  Each block takes up to part_per_thread * blockDim.x queries
+// per round: counts their buckets in shared memory, reserves each
+// non-zero bucket's run with one atomic on the global cursor (the bucket
+// starts from k_part_hist), then places every query at its run's next slot
+// (a shared-memory atomic) and writes it with its input position.
 template <typename K>
 __global__ void __launch_bounds__(kPartThreads) k_part_scatter(const RawOf<K> *__restrict__ q, uint64_t nq,
                                                                PartNorm<K> pn, uint32_t *__restrict__ cursor,
-                                                               RawOf<K> *__restrict__ out_q,
+                                                               uint32_t nb, RawOf<K> *__restrict__ out_q,
                                                                uint32_t *__restrict__ out_i)
 {
     __shared__ PartSmem<K> S;
+    extern __shared__ uint32_t cnt[];
+    constexpr int E = part_per_thread<K>();
     part_load_tables(S, pn);
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
-    for (uint64_t i0 = static_cast<uint64_t>(blockIdx.x) * blockDim.x + (threadIdx.x & ~31u); i0 < nq;
-         i0 += stride * kPartUnroll) {
-        RawOf<K> key[kPartUnroll];
+    const uint64_t round = static_cast<uint64_t>(E) * blockDim.x;
+    for (uint64_t base = blockIdx.x * round; base < nq; base += gridDim.x * round) {
+        for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x) cnt[j] = 0;
+        __syncthreads();
+        RawOf<K> key[E];
+        uint32_t bk[E];
 #pragma unroll
-        for (int u = 0; u < kPartUnroll; ++u) {
-            const uint64_t i = i0 + u * stride + lane;
-            if (i < nq) key[u] = q[i];
+        for (int e = 0; e < E; ++e) {
+            const uint64_t i = base + static_cast<uint64_t>(e) * blockDim.x + threadIdx.x;
+            if (i < nq) key[e] = q[i];
         }
 #pragma unroll
-        for (int u = 0; u < kPartUnroll; ++u) {
-            const uint64_t i = i0 + u * stride + lane;
-            const unsigned vm = __ballot_sync(0xffffffffu, i < nq);
+        for (int e = 0; e < E; ++e) {
+            const uint64_t i = base + static_cast<uint64_t>(e) * blockDim.x + threadIdx.x;
             if (i < nq) {
-                const uint32_t b = part_bucket(S, pn, KeyOps<K>::from_raw(key[u]));
-                const unsigned same = __match_any_sync(vm, b);
-                const int leader = __ffs(same) - 1;
-                uint32_t base = 0;
-                if (lane == leader) base = atomicAdd(cursor + b, static_cast<uint32_t>(__popc(same)));
-                base = __shfl_sync(vm, base, leader);
-                const uint32_t pos = base + __popc(same & part_lanemask_lt());
-                out_q[pos] = key[u];
+                bk[e] = part_bucket(S, pn, KeyOps<K>::from_raw(key[e]));
+                atomicAdd(cnt + bk[e], 1u);
+            }
+        }
+        __syncthreads();
+        {
+            // reserve every non-zero bucket's run: all of a thread's atomics
+            // are issued before any result is used (one round trip)
+            constexpr int RPT = (1 << kMaxPartBits) / kPartThreads;
+            uint32_t cv[RPT];
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+                const uint32_t j = threadIdx.x + k * kPartThreads;
+                cv[k] = j < nb ? cnt[j] : 0u;
+            }
+#pragma unroll
+            for (int k = 0; k < RPT; ++k)
+                if (cv[k]) cv[k] = atomicAdd(cursor + threadIdx.x + k * kPartThreads, cv[k]);
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+                const uint32_t j = threadIdx.x + k * kPartThreads;
+                if (j < nb) cnt[j] = cv[k];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const uint64_t i = base + static_cast<uint64_t>(e) * blockDim.x + threadIdx.x;
+            if (i < nq) {
+                const uint32_t pos = atomicAdd(cnt + bk[e], 1u);
+                out_q[pos] = key[e];
                 out_i[pos] = static_cast<uint32_t>(i);
             }
         }
+        __syncthreads();
     }
 }
 

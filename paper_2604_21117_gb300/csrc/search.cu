@@ -556,7 +556,7 @@ struct WsLayout {
     uint64_t qb, ib, counts, total;
 };
 
-// Bucket counters of the partition: at most 2^kMaxPartBits buckets, plus
+// Bucket totals of the partition: at most 2^kMaxPartBits buckets, plus
 // the ticket word, rounded to whole 16-byte groups.
 constexpr uint64_t kPartCountWords = (1ull << kMaxPartBits) + 4;
 
@@ -803,8 +803,10 @@ static cudaError_t part_sort(const DevTree &t, const RawOf<K> *q, uint64_t nq, c
     pn.r = pp.r;
     pn.cshift = pp.cshift;
     pn.scale = static_cast<float>(1u << pp.r);
-    uint32_t *counts = reinterpret_cast<uint32_t *>(ws + w.counts);
-    cudaError_t e = cudaMemsetAsync(counts, 0, (static_cast<uint64_t>(pp.nb) + 4) * 4, s);
+    pn.split_R = t.split_R;
+    pn.rshift = t.split_rshift;
+    uint32_t *total = reinterpret_cast<uint32_t *>(ws + w.counts);
+    cudaError_t e = cudaMemsetAsync(total, 0, (static_cast<uint64_t>(pp.nb) + 4) * 4, s);
     if (e != cudaSuccess) return e;
     static int sms = 0;
     if (sms == 0) {
@@ -813,11 +815,31 @@ static cudaError_t part_sort(const DevTree &t, const RawOf<K> *q, uint64_t nq, c
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
     }
-    uint64_t grid = (nq + kPartThreads * kPartUnroll - 1) / (kPartThreads * kPartUnroll);
-    const uint64_t cap = 2ull * sms;  // two blocks of 1024 threads per SM
-    if (grid > cap) grid = cap;
-    k_part_count<K><<<static_cast<unsigned>(grid), kPartThreads, 0, s>>>(q, nq, pn, counts, pp.nb);
-    k_part_scatter<K><<<static_cast<unsigned>(grid), kPartThreads, 0, s>>>(q, nq, pn, counts, dst_q, dst_i);
+    constexpr int kMaxDyn = (1 << kMaxPartBits) * 4;
+    static const cudaError_t a1 =
+        cudaFuncSetAttribute(k_part_hist<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDyn);
+    static const cudaError_t a2 =
+        cudaFuncSetAttribute(k_part_scatter<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDyn);
+    if (a1 != cudaSuccess) return a1;
+    if (a2 != cudaSuccess) return a2;
+    const int dyn = static_cast<int>(pp.nb) * 4;
+    // one wave: as many blocks as are resident at the largest bucket count
+    static int occ_h = 0, occ_s = 0;
+    if (occ_h == 0) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_h, k_part_hist<K>, kPartThreads, kMaxDyn);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_s, k_part_scatter<K>, kPartThreads, kMaxDyn);
+        if (e != cudaSuccess) return e;
+        if (occ_h < 1) occ_h = 1;
+        if (occ_s < 1) occ_s = 1;
+    }
+    uint64_t gh = (nq + 4ull * kPartThreads - 1) / (4ull * kPartThreads);
+    if (gh > static_cast<uint64_t>(occ_h) * sms) gh = static_cast<uint64_t>(occ_h) * sms;
+    const uint64_t per_round = static_cast<uint64_t>(part_per_thread<K>()) * kPartThreads;
+    uint64_t gs = (nq + per_round - 1) / per_round;
+    if (gs > static_cast<uint64_t>(occ_s) * sms) gs = static_cast<uint64_t>(occ_s) * sms;
+    k_part_hist<K><<<static_cast<unsigned>(gh), kPartThreads, dyn, s>>>(q, nq, pn, total, pp.nb);
+    k_part_scatter<K><<<static_cast<unsigned>(gs), kPartThreads, dyn, s>>>(q, nq, pn, total, pp.nb, dst_q, dst_i);
     return cudaGetLastError();
 }
 
