@@ -153,7 +153,7 @@ typedef struct bt_search_opts {
      * descent (Sec. IV-A sorts the batch so that queries for one node are
      * adjacent; see bt_sort_batch for the order obtained): -1 lets the
      * library choose from nq (none below 16384 queries), 0 skips the
-     * partition, 1..14 forces that many bits (larger values mean 14). */
+     * partition, 1..13 forces that many bits (larger values mean 13). */
     int32_t sort_bits;
     /* If non-NULL: device array of `height` counters to which the search
      * adds, per level, how many node key blocks it fetched -- the quantity
@@ -197,7 +197,7 @@ bt_status bt_search_batch_ex(const bt_tree *tree, const void *d_queries, uint64_
  * routed to one node are adjacent).  Writes the reordered queries and, for
  * each, its input position.  The order is that of a bucket number monotone
  * in the key, on `sort_bits` bits (-1 = library choice: about nq/16
- * buckets, at most 2^14; 0 = no reordering: the queries are copied and the
+ * buckets, at most 2^13; 0 = no reordering: the queries are copied and the
  * index is the identity):
  *   bucket(q) = (c << r) | s, where c = the number of the tree's splitters
  *   (bt_info.nsplit keys, see bt_build) smaller than q and s = floor(2^r *

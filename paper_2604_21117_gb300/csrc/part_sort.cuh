@@ -44,7 +44,7 @@ namespace btgb {
 constexpr int kSplitSlots = 1023;   // splitters per tree, at most
 constexpr int kRadixBits = 12;      // pre-index of the splitters by leading key bits
 constexpr int kSplitBits = 10;      // bits of c with the full table
-constexpr int kMaxPartBits = 14;    // bucket bits, at most (2^14 counters in shared memory)
+constexpr int kMaxPartBits = 13;    // bucket bits, at most (2^13 counters in shared memory)
 constexpr int kPartThreads = 1024;
 
 // Per-search view of the tree's splitter table.
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(kPartThreads) k_part_hist(const RawOf<K> *__re
     const uint32_t per4 = (groups + blockDim.x - 1) / blockDim.x;  // uint4 groups per thread
     uint4 *t4 = reinterpret_cast<uint4 *>(total);
     const uint32_t g0 = threadIdx.x * per4;
-    uint4 v[4];  // nb <= 2^14 and 1024 threads: at most 4 groups per thread
+    uint4 v[4];  // nb <= 2^13 and 1024 threads: at most 2 groups per thread
     uint32_t sum = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {

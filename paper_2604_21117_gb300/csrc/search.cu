@@ -177,9 +177,9 @@ __device__ __forceinline__ uint32_t child_of(const DevTree &t, int l, uint32_t n
 
 // Stage nu node blocks of CH 16-byte chunks (block i of `src` array at
 // list[i]) into consecutive shared-memory slots with 16-byte asynchronous
-// copies: CH lanes per block when CH <= 32 (32 / CH blocks per round, no
-// divisions), else the warp walks each block.  `.cg` (L2 only) for leaves,
-// `.ca` for inner levels.
+// copies: CH lanes per block when CH <= 32 (32 / CH blocks per round), else
+// the warp walks each block.  `.cg` (L2 only) for leaves, `.ca` for inner
+// levels.  Used by the paper-layout descent (whole nodes).
 template <int CH>
 __device__ __forceinline__ void stage_blocks(unsigned char *dst, const unsigned char *src, uint32_t blk_bytes,
                                              const uint32_t *list, int nu, int lane, bool leaf)
@@ -408,8 +408,16 @@ __global__ void __launch_bounds__(kDescWarpsMax * 32) k_descend(
                     }
                     phase ^= 1u;
                 } else {
-                    stage_blocks<CH>(reinterpret_cast<unsigned char *>(stage), reinterpret_cast<const unsigned char *>(lk),
-                                     M * static_cast<uint32_t>(sizeof(K)), list + rb, nu, lane, last);
+                    for (int i = lane; i < nu * CH; i += 32) {
+                        const int u = i / CH, part = i - u * CH;
+                        const unsigned char *src = reinterpret_cast<const unsigned char *>(
+                                                       lk + static_cast<uint64_t>(list[rb + u]) * M) + part * 16;
+                        unsigned char *dp = reinterpret_cast<unsigned char *>(stage + u * M) + part * 16;
+                        if (last)
+                            cp_async16_cg(dp, src);
+                        else
+                            cp_async16_ca(dp, src);
+                    }
                     cp_async_wait_all();
                 }
                 __syncwarp();
@@ -833,7 +841,9 @@ static cudaError_t part_sort(const DevTree &t, const RawOf<K> *q, uint64_t nq, c
         if (occ_h < 1) occ_h = 1;
         if (occ_s < 1) occ_s = 1;
     }
-    uint64_t gh = (nq + 4ull * kPartThreads - 1) / (4ull * kPartThreads);
+    // at least as many queries per block as buckets, so that clearing and
+    // flushing the block's counters stays a small part of its work
+    uint64_t gh = (nq + 8ull * kPartThreads - 1) / (8ull * kPartThreads);
     if (gh > static_cast<uint64_t>(occ_h) * sms) gh = static_cast<uint64_t>(occ_h) * sms;
     const uint64_t per_round = static_cast<uint64_t>(part_per_thread<K>()) * kPartThreads;
     uint64_t gs = (nq + per_round - 1) / per_round;

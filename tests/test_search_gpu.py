@@ -255,8 +255,8 @@ def _check_sort_contract(bt, tree, keys, q, hsq, hsi, sb):
     nq = q.size
     assert np.array_equal(np.sort(hsi), np.arange(nq, dtype=np.uint32))
     assert np.array_equal(hsq, q[hsi])
-    bits = sb if sb > 0 else ((min(max((nq).bit_length() - 5, 1), 14)) if (sb < 0 and nq >= 16384) else 0)
-    bits = min(bits, 14)
+    bits = sb if sb > 0 else ((min(max((nq).bit_length() - 5, 1), 13)) if (sb < 0 and nq >= 16384) else 0)
+    bits = min(bits, 13)
     if bits <= 0 or keys.size == 0:
         assert np.array_equal(hsi, np.arange(nq, dtype=np.uint32))
         return
