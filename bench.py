@@ -62,6 +62,7 @@ def parse_args(argv=None):
                    help="between timed steps: nothing (default: the 282 MB tree already exceeds the L2 and "
                         "the batches rotate), overwrite a 256 MB buffer, or read one")
     p.add_argument("--staging", type=int, default=0, help="node staging: 0 = 16-byte cp.async, 1 = bulk copy")
+    p.add_argument("--lane-queries", type=int, default=1, help="queries per lane of the descent (1 or 2)")
     p.add_argument("--warps", type=int, default=0, help="descent warps per block (0 = library default)")
     p.add_argument("--pin", type=int, default=-1, help="pinned top-level bytes (-1 = library default)")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -658,6 +659,7 @@ def run_ours(a):
     batches = make_batches(a, keys, pool, rank)
     tree = bt.BTree(keys, vals, a.fanout)
     bt.bt_tree_set_staging(tree.handle, a.staging)
+    bt.bt_tree_set_lane_queries(tree.handle, a.lane_queries)
     if a.warps > 0 or a.pin >= 0:
         bt.bt_tree_set_launch(tree.handle, a.warps if a.warps > 0 else 8, a.pin if a.pin >= 0 else 16384)
     m, kb, vb, B = a.fanout, 8, 8, a.batch
@@ -755,7 +757,7 @@ def run_ours(a):
         "config": {"workload": workload_name(a), "keys": a.keys, "fanout": m, "batch": B,
                    "hit_frac": a.hit, "query_dist": "uniform" if a.zipf is None else f"zipf{a.zipf}",
                    "sort_bits": "auto" if sort_bits < 0 else sort_bits,
-                   "staging": "bulk" if a.staging == 1 else "cp.async",
+                   "staging": "bulk" if a.staging == 1 else "cp.async", "lane_queries": a.lane_queries,
                    "l2": {"write": "flushed before every timed step (256 MB device write)",
                           "read": "flushed before every timed step (256 MB device read)",
                           "none": "not flushed: the 282 MB tree exceeds the 129 MB L2"}[a.l2],

@@ -343,6 +343,7 @@ typedef struct bt_tune {
     uint32_t warps_per_block; /* descent blocks: 4, 8 or 16 warps */
     uint32_t pin_bytes;       /* budget for top levels kept in shared memory (0..49152) */
     uint32_t staging;         /* BT_STAGE_CP_ASYNC or BT_STAGE_BULK */
+    uint32_t lane_queries;    /* queries per lane of the descent: 1 or 2 */
     float us_per_batch;       /* median time of the sample batch with these settings */
 } bt_tune;
 
@@ -358,6 +359,14 @@ bt_status bt_tree_set_launch(bt_tree *tree, uint32_t warps_per_block, uint32_t p
 #define BT_STAGE_BULK 1
 bt_status bt_tree_set_staging(bt_tree *tree, uint32_t mode);
 
+/* Queries each lane carries through the plain descent: 1 (a warp walks 32
+ * consecutive queries of the batch down the tree together, the default) or
+ * 2 (64 per warp: the per-level warp work -- finding the distinct nodes,
+ * staging them -- is shared by twice as many queries; cp.async staging).
+ * Results are identical; speed differs.  Not used by the learned descent.
+ * BT_ERR_ARG on other values. */
+bt_status bt_tree_set_lane_queries(bt_tree *tree, uint32_t per_lane);
+
 /* BT_ERR_TIMEOUT if a bounded device wait of a search gave up since the
  * last call (the results of such a search are invalid), else BT_OK; clears
  * the counter.  Synchronous. */
@@ -367,7 +376,8 @@ bt_status bt_check_timeouts(void);
  * bt_autotune -- build the tree at every fanout in {8, 16, 32, 64} and time
  * a sample batch (d_sample, nsample device queries) through bt_search_batch
  * for every combination of warps per block {4, 8, 16} and pinned bytes
- * {0, 16384, 49152} and both staging modes; keep the fastest.  *out receives the tree built with
+ * {0, 16384, 49152}, both staging modes and 1 or 2 queries per lane; keep
+ * the fastest.  *out receives the tree built with
  * the best fanout and launch parameters applied, *best the choice and its
  * time.  Synchronizes `stream`.  Errors: as bt_build, plus BT_ERR_ARG.
  */

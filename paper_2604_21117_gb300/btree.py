@@ -38,7 +38,7 @@ EXPORTED = ("bt_build", "bt_free", "bt_tree_info", "bt_tree_copy_image", "bt_sea
             "bt_learned_descend_sorted", "bt_learned_search_batch", "bt_model_copy_err_bounds",
             "bt_forest_create", "bt_forest_free",
             "bt_forest_workspace_bytes", "bt_forest_search", "bt_tree_set_launch", "bt_tree_set_staging",
-            "bt_check_timeouts", "bt_autotune", "bt_paper_node_bytes", "bt_paper_layout_build",
+            "bt_tree_set_lane_queries", "bt_check_timeouts", "bt_autotune", "bt_paper_node_bytes", "bt_paper_layout_build",
             "bt_paper_search_batch", "bt_paper_descend_sorted",
             "bt_server_create", "bt_server_submit", "bt_server_poll", "bt_server_drain", "bt_server_get_stats",
             "bt_server_destroy", "bt_server_run_trace")
@@ -340,7 +340,8 @@ class bt_batch_desc(ctypes.Structure):
 
 class bt_tune(ctypes.Structure):
     _fields_ = [("fanout", ctypes.c_uint32), ("warps_per_block", ctypes.c_uint32), ("pin_bytes", ctypes.c_uint32),
-                ("staging", ctypes.c_uint32), ("us_per_batch", ctypes.c_float)]
+                ("staging", ctypes.c_uint32), ("lane_queries", ctypes.c_uint32),
+                ("us_per_batch", ctypes.c_float)]
 
 
 BATCH_DESC_DTYPE = np.dtype([("tree", np.uint32), ("count", np.uint32), ("offset", np.uint64)])
@@ -357,6 +358,8 @@ _lib.bt_tree_set_launch.restype = _i
 _lib.bt_tree_set_launch.argtypes = [_vp, ctypes.c_uint32, ctypes.c_uint32]
 _lib.bt_tree_set_staging.restype = _i
 _lib.bt_tree_set_staging.argtypes = [_vp, ctypes.c_uint32]
+_lib.bt_tree_set_lane_queries.restype = _i
+_lib.bt_tree_set_lane_queries.argtypes = [_vp, ctypes.c_uint32]
 _lib.bt_check_timeouts.restype = _i
 _lib.bt_check_timeouts.argtypes = []
 _lib.bt_autotune.restype = _i
@@ -396,6 +399,10 @@ BT_STAGE_BULK = 1
 
 def bt_tree_set_staging(tree: int, mode: int) -> None:
     _check("bt_tree_set_staging", _lib.bt_tree_set_staging(tree, mode))
+
+
+def bt_tree_set_lane_queries(tree: int, per_lane: int) -> None:
+    _check("bt_tree_set_lane_queries", _lib.bt_tree_set_lane_queries(tree, per_lane))
 
 
 def bt_check_timeouts() -> None:

@@ -35,6 +35,7 @@ struct DevTree {
     uint32_t pin_bytes;  // bytes from the root's block to the end of those levels
     int warps;           // warps per descent block
     int staging;         // 0: 16-byte cp.async per lane, 1: one bulk copy (TMA) per node block
+    int lane_queries;    // queries per lane of the plain descent: 1 (32 per warp) or 2 (64 per warp)
     // Splitters of the batch partition: the largest keys of nsplit evenly
     // spaced leaves, and nsplit + 1 reciprocal widths of the key segments
     // they bound (part_sort.cuh).

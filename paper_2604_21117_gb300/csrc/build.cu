@@ -102,6 +102,13 @@ extern "C" bt_status bt_tree_set_launch(bt_tree *t, uint32_t warps_per_block, ui
     return BT_OK;
 }
 
+extern "C" bt_status bt_tree_set_lane_queries(bt_tree *t, uint32_t per_lane)
+{
+    if (!t || per_lane < 1 || per_lane > 2) return BT_ERR_ARG;
+    t->dev.lane_queries = static_cast<int>(per_lane);
+    return BT_OK;
+}
+
 extern "C" bt_status bt_tree_set_staging(bt_tree *t, uint32_t mode)
 {
     if (!t || mode > 1) return BT_ERR_ARG;
@@ -216,6 +223,7 @@ extern "C" bt_status bt_build(const void *h_keys, const void *h_vals, uint64_t n
     // Descent launch defaults: 8 warps per block, top levels up to 16 KB
     // kept in shared memory (bt_tree_set_launch / bt_autotune change them).
     d.warps = 8;
+    d.lane_queries = 1;
     set_pin_levels(d, t->info, 16384);
 
     // Shape arithmetic: children (or keys, for leaves) per node.

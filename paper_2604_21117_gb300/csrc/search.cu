@@ -454,6 +454,152 @@ __global__ void __launch_bounds__(kDescWarpsMax * 32) k_descend(
     }
 }
 
+// ------------------------------- two queries per lane (64-query chunks)
+//
+// The same level-wise descent with each warp taking 64 consecutive queries
+// of the batch (lane l holds queries l and 32 + l): every per-level warp
+// step -- finding the distinct nodes, staging them, the synchronisations --
+// is shared by twice as many queries, and each lane runs two independent
+// binary searches.  Selected per tree with bt_tree_set_lane_queries.
+
+// Distinct node ids among the warp's 64 (a, b) pairs, as warp_distinct.  A
+// node range wider than 32 lists the distinct a's, then the distinct b's
+// (a node in both sets is then listed, and staged, twice).
+__device__ __forceinline__ void warp_distinct2(uint32_t a, uint32_t b, int lane, uint32_t *list, int &U, int &sa,
+                                               int &sb)
+{
+    const uint32_t nmin = __reduce_min_sync(0xffffffffu, a < b ? a : b);
+    const uint32_t nmax = __reduce_max_sync(0xffffffffu, a < b ? b : a);
+    if (nmax - nmin < 32u) {
+        const unsigned ba = 1u << (a - nmin), bb = 1u << (b - nmin);
+        const unsigned mask = __reduce_or_sync(0xffffffffu, ba | bb);
+        U = __popc(mask);
+        sa = __popc(mask & (ba - 1u));
+        sb = __popc(mask & (bb - 1u));
+        if ((mask >> lane) & 1u) list[__popc(mask & ((1u << lane) - 1u))] = nmin + lane;
+    } else {
+        const unsigned same_a = __match_any_sync(0xffffffffu, a);
+        const unsigned same_b = __match_any_sync(0xffffffffu, b);
+        const int lead_a = __ffs(same_a) - 1, lead_b = __ffs(same_b) - 1;
+        const unsigned leaders_a = __ballot_sync(0xffffffffu, lane == lead_a);
+        const unsigned leaders_b = __ballot_sync(0xffffffffu, lane == lead_b);
+        const int ua = __popc(leaders_a);
+        U = ua + __popc(leaders_b);
+        sa = __popc(leaders_a & ((1u << lead_a) - 1u));
+        sb = ua + __popc(leaders_b & ((1u << lead_b) - 1u));
+        if (lane == lead_a) list[sa] = a;
+        if (lane == lead_b) list[sb] = b;
+    }
+}
+
+template <typename K, int M>
+constexpr int desc2_smem_per_warp()
+{
+    return stage_slots<K, M>() * M * static_cast<int>(sizeof(K)) + 64 * 4;
+}
+
+template <typename K, typename V, int M, bool COUNT>
+__global__ void __launch_bounds__(kDescWarpsMax * 32) k_descend2(
+    const DevTree t, const RawOf<K> *__restrict__ q, const uint32_t *__restrict__ qidx, uint64_t nq,
+    V *__restrict__ out_v, uint8_t *__restrict__ out_f, unsigned long long *__restrict__ fetch)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int CH = M * static_cast<int>(sizeof(K)) / 16;
+    constexpr int SLOTS = stage_slots<K, M>();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint32_t pin_bytes = t.pin_bytes;
+    unsigned char *pin = smem;
+    K *stage = reinterpret_cast<K *>(smem + pin_bytes) + warp * SLOTS * M;
+    uint32_t *list =
+        reinterpret_cast<uint32_t *>(smem + pin_bytes + static_cast<uint32_t>(nw) * SLOTS * M * sizeof(K)) + warp * 64;
+    const unsigned char *top = static_cast<const unsigned char *>(t.keys[0]);
+    for (uint32_t i = threadIdx.x * 16u; i < pin_bytes; i += blockDim.x * 16u) cp_async16_ca(pin + i, top + i);
+    cp_async_wait_all();
+    __syncthreads();
+
+    const uint64_t nchunks = (nq + 63) / 64;
+    const uint64_t stride = static_cast<uint64_t>(gridDim.x) * nw;
+    const int H = t.height, P = t.pin_levels;
+    for (uint64_t c = static_cast<uint64_t>(blockIdx.x) * nw + warp; c < nchunks; c += stride) {
+        // tail lanes follow the chunk's first query so they never add a node fetch
+        const uint64_t pa = c * 64 + lane, pb = pa + 32;
+        const bool va = pa < nq, vb = pb < nq;
+        const K ka = KeyOps<K>::load(q, va ? pa : c * 64);
+        const K kb = KeyOps<K>::load(q, vb ? pb : c * 64);
+        const uint32_t da = va ? (qidx ? qidx[pa] : static_cast<uint32_t>(pa)) : 0u;
+        const uint32_t db = vb ? (qidx ? qidx[pb] : static_cast<uint32_t>(pb)) : 0u;
+        uint32_t na = 0, nb = 0;
+        int l = 0;
+        for (; l < P; ++l) {
+            if (COUNT) {
+                int U, sa, sb;
+                warp_distinct2(na, nb, lane, list, U, sa, sb);
+                __syncwarp();
+                if (lane == 0) atomicAdd(fetch + l, static_cast<unsigned long long>(U));
+            }
+            const K *lvl = reinterpret_cast<const K *>(pin + (static_cast<const unsigned char *>(t.keys[l]) - top));
+            const int r_a = block_rank<K, M>(lvl + static_cast<uint64_t>(na) * M, ka);
+            const int r_b = block_rank<K, M>(lvl + static_cast<uint64_t>(nb) * M, kb);
+            na = child_of(t, l, na, r_a);
+            nb = child_of(t, l, nb, r_b);
+        }
+        for (; l < H; ++l) {
+            const K *lk = static_cast<const K *>(t.keys[l]);
+            const bool last = (l + 1 == H);
+            int U, sa, sb;
+            warp_distinct2(na, nb, lane, list, U, sa, sb);
+            if (COUNT && lane == 0) atomicAdd(fetch + l, static_cast<unsigned long long>(U));
+            __syncwarp();
+            int r_a = 0, r_b = 0;
+            bool e_a = false, e_b = false;
+            for (int rb = 0; rb < U; rb += SLOTS) {
+                const int nu = (U - rb < SLOTS) ? U - rb : SLOTS;
+                for (int i = lane; i < nu * CH; i += 32) {
+                    const int u = i / CH, part = i - u * CH;
+                    const unsigned char *src =
+                        reinterpret_cast<const unsigned char *>(lk + static_cast<uint64_t>(list[rb + u]) * M) + part * 16;
+                    unsigned char *dp = reinterpret_cast<unsigned char *>(stage + u * M) + part * 16;
+                    if (last)
+                        cp_async16_cg(dp, src);
+                    else
+                        cp_async16_ca(dp, src);
+                }
+                cp_async_wait_all();
+                __syncwarp();
+                if (sa >= rb && sa < rb + nu) {
+                    const K *blk = stage + (sa - rb) * M;
+                    r_a = block_rank<K, M>(blk, ka);
+                    e_a = (blk[r_a] == ka);
+                }
+                if (sb >= rb && sb < rb + nu) {
+                    const K *blk = stage + (sb - rb) * M;
+                    r_b = block_rank<K, M>(blk, kb);
+                    e_b = (blk[r_b] == kb);
+                }
+                __syncwarp();
+            }
+            if (!last) {
+                na = child_of(t, l, na, r_a);
+                nb = child_of(t, l, nb, r_b);
+            } else {
+                const V *vals = static_cast<const V *>(t.vals);
+                const bool hit_a = (static_cast<uint64_t>(r_a) < t.cbase[l] + (na < t.crem[l] ? 1u : 0u)) && e_a;
+                const bool hit_b = (static_cast<uint64_t>(r_b) < t.cbase[l] + (nb < t.crem[l] ? 1u : 0u)) && e_b;
+                const V v_a = hit_a ? vals[static_cast<uint64_t>(na) * M + r_a] : static_cast<V>(~static_cast<V>(0));
+                const V v_b = hit_b ? vals[static_cast<uint64_t>(nb) * M + r_b] : static_cast<V>(~static_cast<V>(0));
+                if (va) {
+                    out_v[da] = v_a;
+                    out_f[da] = hit_a ? 1 : 0;
+                }
+                if (vb) {
+                    out_v[db] = v_b;
+                    out_f[db] = hit_b ? 1 : 0;
+                }
+            }
+        }
+    }
+}
+
 // ---------------------------------------- the paper's node layout (Eq. 1)
 //
 // The same level-wise descent over the array-of-nodes layout of Eq. 1: the
@@ -654,11 +800,46 @@ static cudaError_t launch_descend(const DescendArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+template <typename K, typename V, int M, bool COUNT>
+static cudaError_t launch_descend2(const DescendArgs &a, cudaStream_t s)
+{
+    const int nw = a.t->warps > 0 ? a.t->warps : kDescWarpsDefault;
+    auto kern = k_descend2<K, V, M, COUNT>;
+    const int smem = static_cast<int>(a.t->pin_bytes) + nw * desc2_smem_per_warp<K, M>();
+    static const cudaError_t attr = cudaFuncSetAttribute(
+        kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kPinBudgetMax + kDescWarpsMax * desc2_smem_per_warp<K, M>());
+    if (attr != cudaSuccess) return attr;
+    constexpr int kCache = kPinBudgetMax / 256 + 2;
+    static int occ_cache[kDescWarpsMax + 1][kCache] = {{0}};
+    const int key = (static_cast<int>(a.t->pin_bytes) + 255) / 256;
+    if (occ_cache[nw][key] == 0) {
+        int b = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, nw * 32,
+                                                                      key * 256 + nw * desc2_smem_per_warp<K, M>());
+        if (e != cudaSuccess) return e;
+        occ_cache[nw][key] = b > 0 ? b : 1;
+    }
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    uint64_t grid = ((a.nq + 63) / 64 + nw - 1) / nw;
+    const uint64_t cap = static_cast<uint64_t>(sms) * occ_cache[nw][key];
+    if (grid > cap) grid = cap;
+    kern<<<static_cast<unsigned>(grid), nw * 32, smem, s>>>(*a.t, static_cast<const RawOf<K> *>(a.q), a.qidx, a.nq,
+                                                          static_cast<V *>(a.out_v), a.out_f, a.fetch);
+    return cudaGetLastError();
+}
+
 template <typename K, typename V, int M>
 static cudaError_t dispatch_mode(const DescendArgs &a, cudaStream_t s)
 {
     if constexpr (!std::is_same<K, Key32>::value) {
         if (a.md) return launch_descend<K, V, M, false, true>(a, s);
+    }
+    if (a.t->lane_queries == 2) {
+        if (a.fetch) return launch_descend2<K, V, M, true>(a, s);
+        return launch_descend2<K, V, M, false>(a, s);
     }
     if (a.fetch) return launch_descend<K, V, M, true, false>(a, s);
     return launch_descend<K, V, M, false, false>(a, s);

@@ -2,8 +2,9 @@
 //
 // For a key set and a sample batch, every fanout in {8, 16, 32, 64} is
 // built and the sample searched with every combination of warps per block
-// {4, 8, 16}, shared-memory pin budget {0, 16 KB, 48 KB} and node staging
-// mode (16-byte cp.async or bulk copy); the fastest
+// {4, 8, 16}, shared-memory pin budget {0, 16 KB, 48 KB}, node staging
+// mode (16-byte cp.async or bulk copy) and queries per lane {1, 2}; the
+// fastest
 // combination (median of timed repetitions, CUDA events on the caller's
 // stream) wins and its tree is returned with those settings applied.
 #include <cuda_runtime.h>
@@ -77,7 +78,7 @@ extern "C" bt_status bt_autotune(const void *h_keys, const void *h_vals, uint64_
     const uint32_t warps[] = {4, 8, 16};
     const uint32_t pins[] = {0, 16384, 49152};
     bt_tree *keep = nullptr;
-    bt_tune b{0, 0, 0, 0, 0.0f};
+    bt_tune b{0, 0, 0, 0, 1, 0.0f};
     for (uint32_t m : fanouts) {
         bt_tree *t = nullptr;
         bt_status st = bt_build(h_keys, h_vals, n, key_w, val_w, m, stream, &t);
@@ -93,9 +94,12 @@ extern "C" bt_status bt_autotune(const void *h_keys, const void *h_vals, uint64_
         bool won = false;
         for (uint32_t w : warps)
             for (uint32_t p : pins)
-                for (uint32_t sm = 0; sm <= 1; ++sm) {
+                for (uint32_t cfg = 0; cfg < 3; ++cfg) {
+                // (staging, queries per lane): (cp.async, 1), (bulk, 1), (cp.async, 2)
+                const uint32_t sm = cfg == 1 ? 1u : 0u, lq = cfg == 2 ? 2u : 1u;
                 bt_tree_set_launch(t, w, p);
                 bt_tree_set_staging(t, sm);
+                bt_tree_set_lane_queries(t, lq);
                 float us = 0;
                 st = time_search(t, d_sample, nsample, sc, ws_bytes, s, &us);
                 if (st != BT_OK) {
@@ -104,7 +108,7 @@ extern "C" bt_status bt_autotune(const void *h_keys, const void *h_vals, uint64_
                     return st;
                 }
                 if (b.fanout == 0 || us < b.us_per_batch) {
-                    b = bt_tune{m, w, p, sm, us};
+                    b = bt_tune{m, w, p, sm, lq, us};
                     won = true;
                 }
             }
@@ -117,6 +121,7 @@ extern "C" bt_status bt_autotune(const void *h_keys, const void *h_vals, uint64_
     }
     bt_tree_set_launch(keep, b.warps_per_block, b.pin_bytes);
     bt_tree_set_staging(keep, b.staging);
+    bt_tree_set_lane_queries(keep, b.lane_queries);
     *out = keep;
     *best = b;
     return BT_OK;

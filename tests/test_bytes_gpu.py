@@ -106,12 +106,13 @@ def test_bulk_staging(bt, m):
     bt.bt_check_timeouts()
 
 
-@pytest.mark.parametrize("warps,pin", [(4, 0), (16, 49152)])
-def test_launch_settings(bt, warps, pin):
+@pytest.mark.parametrize("warps,pin,lq", [(4, 0, 1), (16, 49152, 1), (8, 16384, 2)])
+def test_launch_settings(bt, warps, pin, lq):
     keys = W.byte_keys(80_000, 32, seed=940)
     vals = W.rank_values(keys.shape[0], 64)
     tree = bt.BTree(keys, vals, 16)
     bt.bt_tree_set_launch(tree.handle, warps, pin)
+    bt.bt_tree_set_lane_queries(tree.handle, lq)
     o = OracleBytesTree(keys, vals, 16)
     _check(bt, tree, o, W.make_byte_queries(keys, 25_000, 0.6, seed=941))
 

@@ -102,15 +102,17 @@ def test_forest_search_replays_from_a_cuda_graph(bt):
     bt.bt_forest_free(forest)
 
 
-@pytest.mark.parametrize("warps,pin,staging", [(4, 0, 0), (16, 0, 0), (4, 49152, 0), (16, 49152, 0),
-                                               (8, 16384, 0), (4, 0, 1), (16, 49152, 1), (8, 16384, 1)])
-def test_launch_settings_do_not_change_results(bt, warps, pin, staging):
+@pytest.mark.parametrize("warps,pin,staging,lq", [(4, 0, 0, 1), (16, 0, 0, 1), (4, 49152, 0, 1), (16, 49152, 0, 1),
+                                                  (8, 16384, 0, 1), (4, 0, 1, 1), (16, 49152, 1, 1), (8, 16384, 1, 1),
+                                                  (8, 16384, 0, 2), (4, 0, 0, 2), (16, 49152, 0, 2)])
+def test_launch_settings_do_not_change_results(bt, warps, pin, staging, lq):
     keys = W.uniform_keys(500_000, 64, seed=63)
     vals = W.rank_values(keys.size, 64)
     tree = bt.BTree(keys, vals, 16)
     o = OracleTree(keys, vals, 16)
     bt.bt_tree_set_launch(tree.handle, warps, pin)
     bt.bt_tree_set_staging(tree.handle, staging)
+    bt.bt_tree_set_lane_queries(tree.handle, lq)
     q = W.make_queries(keys, 70_001, 0.9, seed=64, width_bits=64)
     import torch
     v, f = tree.search(torch.from_numpy(q).cuda())
@@ -144,10 +146,29 @@ def test_autotune_returns_a_correct_tree(bt):
     h, best = bt.bt_autotune(keys, vals, torch.from_numpy(sample).cuda(), sample.size)
     tree = bt.BTree(None, None, handle=h)
     assert best.fanout in (8, 16, 32, 64) and best.warps_per_block in (4, 8, 16)
-    assert best.pin_bytes in (0, 16384, 49152) and best.staging in (0, 1) and best.us_per_batch > 0
+    assert best.pin_bytes in (0, 16384, 49152) and best.staging in (0, 1) and best.lane_queries in (1, 2)
+    assert best.us_per_batch > 0
     assert tree.fanout == best.fanout
     o = OracleTree(keys, vals, best.fanout)
     q = W.make_queries(keys, 30_000, 0.8, seed=67, width_bits=64)
     v, f = tree.search(torch.from_numpy(q).cuda())
     ov, of, _, _ = o.search(q)
     assert np.array_equal(v.cpu().numpy(), ov) and np.array_equal(f.cpu().numpy(), of)
+
+
+@pytest.mark.parametrize("m,kw,vw", [(8, 32, 32), (16, 64, 64), (32, 64, 32), (64, 32, 64)])
+@pytest.mark.parametrize("nq", [1, 33, 63, 64, 65, 20_011])
+def test_two_queries_per_lane(bt, m, kw, vw, nq):
+    """64-query chunks: every fanout and width, ragged sizes, sorted and
+    unsorted order, narrow and wide node ranges per warp."""
+    import torch
+    keys = W.uniform_keys(200_000, kw, seed=71 + m)
+    vals = W.rank_values(keys.size, vw)
+    tree = bt.BTree(keys, vals, m)
+    bt.bt_tree_set_lane_queries(tree.handle, 2)
+    o = OracleTree(keys, vals, m, val_bits=vw)
+    q = W.make_queries(keys, nq, 0.8, seed=72 + nq, width_bits=kw, zipf_s=1.1)
+    ov, of, _, _ = o.search(q)
+    for sb in (-1, 0, 6):
+        v, f = tree.search(torch.from_numpy(q).cuda(), sort_bits=sb)
+        assert np.array_equal(v.cpu().numpy().astype(np.uint64), ov) and np.array_equal(f.cpu().numpy(), of), sb
