@@ -43,7 +43,11 @@ L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes of one descent launch on the default workload, from one ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum), valid only while
 # the kernel source is the one captured (sha256 prefix of csrc/search.cu).
-NCU_DESCEND_TRAFFIC = {"search_cu_sha256": None, "bytes_per_launch": None}
+# DRAM bytes (read + write) of one k_descend launch on the default workload,
+# from the ncu capture summarised in profiles/k_descend_2p24keys_b2p20.md;
+# valid only while the descent's source (search.cu up to the end of
+# k_descend) hashes to the same value.
+NCU_DESCEND_TRAFFIC = {"descend_src_sha256": "fea72898763be543", "bytes_per_launch": 216395008 + 3636224}
 
 
 def parse_args(argv=None):
@@ -226,8 +230,13 @@ class ClockSampler:
 
 
 def src_sha256() -> str:
-    with open(os.path.join(ROOT, "paper_2604_21117_gb300", "csrc", "search.cu"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    """Hash of the descent's source: search.cu from its descent section to the
+    end of k_descend."""
+    with open(os.path.join(ROOT, "paper_2604_21117_gb300", "csrc", "search.cu")) as f:
+        txt = f.read()
+    a = txt.find("// -------------------------------------------- level-wise descent (a3-a5)")
+    b = txt.find("// ------------------------------- two queries per lane")
+    return hashlib.sha256(txt[a:b].encode()).hexdigest()[:16] if a >= 0 and b > a else ""
 
 
 # ------------------------------------------------------------ dist
@@ -740,7 +749,10 @@ def run_ours(a):
     achieved = statistics.fmean(desc_bytes) / (statistics.fmean(desc_ms) / 1e3) / 1e9
     peak, peak_kind = measured_peaks()
     traffic = None
-    if NCU_DESCEND_TRAFFIC["search_cu_sha256"] == src_sha256():
+    default_workload = (a.keys == 1 << 24 and a.batch == 1 << 20 and a.fanout == 32 and a.zipf is None
+                        and abs(a.hit - 0.9) < 1e-9)
+    if (NCU_DESCEND_TRAFFIC["descend_src_sha256"] == src_sha256() and default_workload and a.lane_queries == 1
+            and a.staging == 0 and a.warps <= 0 and a.pin < 0 and a.sort_bits < 0):
         traffic = NCU_DESCEND_TRAFFIC["bytes_per_launch"]
     step_gbs = statistics.fmean(node_bytes) / (statistics.fmean(step_ms) / 1e3) / 1e9
     sort_k = bt.bt_sort_launches(tree.handle, B, sort_bits)

@@ -123,7 +123,9 @@ typedef struct bt_info {
  * (segment 0 starts at the smallest key, the last ends at the largest); for
  * 32-byte keys lo and hi are the big-endian values of the 8 bytes after the
  * p bytes the segment's bounds share (p <= 24), and nsplit + 1 bytes p
- * follow.
+ * follow; then 4097 uint16 R[j] = the number of splitters whose leading 12
+ * bits above the smallest key are below j (32-byte keys: bits of the 8 bytes
+ * after the bytes all keys share).
  *
  * Errors: BT_ERR_ARG, BT_ERR_FANOUT, BT_ERR_UNSORTED, BT_ERR_DUPLICATE,
  * BT_ERR_NOMEM, BT_ERR_CUDA.  *out is set only on BT_OK.

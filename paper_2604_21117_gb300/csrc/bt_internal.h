@@ -42,8 +42,10 @@ struct DevTree {
     const void *split;
     const float *split_inv;
     const unsigned char *split_off;  // 32-byte keys: bytes shared within each segment
-    const uint16_t *split_R;         // integer keys: splitter pre-index by leading key bits
+    const uint16_t *split_R;         // splitter pre-index by leading key bits
     int split_rshift;
+    int split_p0;                    // 32-byte keys: bytes all keys share (leading bits follow them)
+    uint64_t split_wmin;             // 32-byte keys: the 8 bytes after them in the smallest key
     uint32_t nsplit;
 };
 

@@ -211,10 +211,9 @@ extern "C" bt_status bt_build(const void *h_keys, const void *h_vals, uint64_t n
         if (kb == 32) {
             split_off_offset = off;
             off = align_up(off + static_cast<uint64_t>(nsplit) + 1, 256);
-        } else {
-            split_R_offset = off;
-            off = align_up(off + ((1ull << 12) + 1) * 2, 256);
         }
+        split_R_offset = off;
+        off = align_up(off + ((1ull << 12) + 1) * 2, 256);
     }
     t->info.nsplit = nsplit;
     d.nsplit = nsplit;
@@ -292,18 +291,32 @@ extern "C" bt_status bt_build(const void *h_keys, const void *h_vals, uint64_t n
             }
             sinv[c] = static_cast<float>(1.0 / (width + 1.0));
         }
-        if (kb != 32) {
-            // pre-index: R[j] = splitters whose leading 12 bits above kmin are < j
-            const uint64_t range = d.kmax - d.kmin;
-            int rl = 0;
-            while (rl < 64 && (range >> rl) != 0) ++rl;
-            d.split_rshift = rl > 12 ? rl - 12 : 0;
-            uint16_t *R = reinterpret_cast<uint16_t *>(img + split_R_offset);
-            uint32_t c = 0;
-            for (uint32_t j = 0; j <= (1u << 12); ++j) {
-                while (c < nsplit && ((load_uint(sk, c, kb) - d.kmin) >> d.split_rshift) < j) ++c;
-                R[j] = static_cast<uint16_t>(c);
+        // pre-index: R[j] = splitters whose leading 12 bits above the smallest
+        // key are < j.  32-byte keys take those bits from the 8 bytes after
+        // the p0 bytes every key shares.
+        int p0 = 0;
+        uint64_t wmin = d.kmin, wmax = d.kmax;
+        if (kb == 32) {
+            const unsigned char *a = key_ptr(h_keys, 0, kb), *b = key_ptr(h_keys, n - 1, kb);
+            while (p0 < 24 && a[p0] == b[p0]) ++p0;
+            wmin = be64(a + p0);
+            wmax = be64(b + p0);
+        }
+        d.split_p0 = p0;
+        d.split_wmin = wmin;
+        const uint64_t range = wmax - wmin;
+        int rl = 0;
+        while (rl < 64 && (range >> rl) != 0) ++rl;
+        d.split_rshift = rl > 12 ? rl - 12 : 0;
+        uint16_t *R = reinterpret_cast<uint16_t *>(img + split_R_offset);
+        uint32_t c = 0;
+        for (uint32_t j = 0; j <= (1u << 12); ++j) {
+            while (c < nsplit) {
+                const uint64_t w = kb == 32 ? be64(key_ptr(h_keys, sidx[c], kb) + p0) : load_uint(sk, c, kb);
+                if (((w - wmin) >> d.split_rshift) >= j) break;
+                ++c;
             }
+            R[j] = static_cast<uint16_t>(c);
         }
     }
     // Inner levels bottom-up: separator j = largest key under child j.
@@ -349,8 +362,7 @@ extern "C" bt_status bt_build(const void *h_keys, const void *h_vals, uint64_t n
     d.split = static_cast<unsigned char *>(t->d_image) + t->info.split_offset;
     d.split_inv = reinterpret_cast<const float *>(static_cast<unsigned char *>(t->d_image) + t->info.split_inv_offset);
     d.split_off = kb == 32 ? static_cast<unsigned char *>(t->d_image) + split_off_offset : nullptr;
-    d.split_R = kb == 32 ? nullptr
-                         : reinterpret_cast<const uint16_t *>(static_cast<unsigned char *>(t->d_image) + split_R_offset);
+    d.split_R = reinterpret_cast<const uint16_t *>(static_cast<unsigned char *>(t->d_image) + split_R_offset);
     t->info.d_image = t->d_image;
     *out = t;
     return BT_OK;

@@ -53,8 +53,10 @@ struct PartNorm {
     const K *split;         // nsplit splitters, ascending (device)
     const float *split_inv; // nsplit + 1 reciprocal segment widths (device)
     const unsigned char *split_off;  // 32-byte keys: per segment, bytes its keys share
-    const uint16_t *split_R;         // integer keys: R[j] = splitters whose leading bits are < j
+    const uint16_t *split_R;         // R[j] = splitters whose leading bits are < j
     int rshift;                      // leading bits = (key - kmin) >> rshift
+    int p0;                          // 32-byte keys: bytes every key shares; leading bits taken
+    uint64_t wmin;                   //   from (8 bytes after them) - (the same of kmin)
     K kmin;                 // smallest key: lower bound of segment 0
     K kmax;                 // largest key: upper bound of the last segment
     uint32_t nsplit;
@@ -131,9 +133,29 @@ __device__ __forceinline__ uint64_t key32_window(const Key32 &k, int p)
 __device__ __forceinline__ uint32_t part_bucket(const PartSmem<Key32> &S, const PartNorm<Key32> &pn, const Key32 &q)
 {
     uint32_t c = 0;
+    if (pn.split_R) {
+        if (pn.kmax < q) {
+            c = pn.nsplit;
+        } else if (!(q < pn.kmin)) {
+            // inside [kmin, kmax] every key shares the first p0 bytes, so the
+            // next 8 bytes order q among the splitters
+            const uint64_t j64 = (key32_window(q, pn.p0) - pn.wmin) >> pn.rshift;
+            const uint32_t j = j64 < (1u << kRadixBits) ? static_cast<uint32_t>(j64) : (1u << kRadixBits) - 1u;
+            uint32_t lo = S.R[j], hi = S.R[j + 1];
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (S.sp[mid] < q)
+                    lo = mid + 1;
+                else
+                    hi = mid;
+            }
+            c = lo;
+        }
+    } else {
 #pragma unroll
-    for (uint32_t h = (kSplitSlots + 1) / 2; h >= 1; h >>= 1)
-        if (S.sp[c + h - 1] < q) c += h;
+        for (uint32_t h = (kSplitSlots + 1) / 2; h >= 1; h >>= 1)
+            if (S.sp[c + h - 1] < q) c += h;
+    }
     if (pn.r == 0) return c >> pn.cshift;
     const uint32_t top = (1u << pn.r) - 1u;
     const Key32 lo = c ? S.sp[c - 1] : pn.kmin;

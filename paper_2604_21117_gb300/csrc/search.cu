@@ -994,6 +994,8 @@ static cudaError_t part_sort(const DevTree &t, const RawOf<K> *q, uint64_t nq, c
     pn.scale = static_cast<float>(1u << pp.r);
     pn.split_R = t.split_R;
     pn.rshift = t.split_rshift;
+    pn.p0 = t.split_p0;
+    pn.wmin = t.split_wmin;
     uint32_t *total = reinterpret_cast<uint32_t *>(ws + w.counts);
     cudaError_t e = cudaMemsetAsync(total, 0, (static_cast<uint64_t>(pp.nb) + 4) * 4, s);
     if (e != cudaSuccess) return e;
