@@ -75,6 +75,7 @@ def parse_args(argv=None):
     p.add_argument("--no-batching", action="store_true", help="skip the multi-tree batching leg")
     p.add_argument("--no-serving", action="store_true", help="skip the serving leg")
     p.add_argument("--no-paper-keys", action="store_true", help="skip the 32-byte-key leg")
+    p.add_argument("--no-sweeps", action="store_true", help="skip the batch-size and tree-size sweeps")
     return p.parse_args(argv)
 
 
@@ -484,6 +485,49 @@ def paper_keys_leg(a, bt, flush, stream, peak):
                            "kind": "oracle", "sample": f"{sample.shape[0]} queries of the same mix"}
     o.close()
     return res
+
+
+# ------------------------------------------------------ sweeps
+
+def sweep_leg(a, bt, stream, keys, vals, tree):
+    """The configured sweeps: batch sizes 1, 16, 64, 256, 1024 and 2^20 on the
+    2^24-key tree (uniform and Zipf(1.1) queries, 90% hits), and tree sizes
+    10 to 2e7 keys (fanout 32) at batch 1024.  Lookups/s and p50/p99 of
+    bt_search_batch per call, every result checked against numpy's binary
+    search over the keys."""
+    import torch
+
+    def run(t, k, v, B, z, seed, calls):
+        qh = W.make_queries(k, B, 0.9, seed=seed, width_bits=64, zipf_s=z)
+        q = torch.from_numpy(qh).cuda()
+        nb = t.workspace_bytes(B)
+        ws = torch.empty(max(nb, 1), dtype=torch.uint8, device="cuda")
+        ov, of = t.alloc_outputs(B)
+        fn = lambda: bt.bt_search_batch(t.handle, q, B, ov, of, ws, nb, stream)
+        for _ in range(3):
+            fn()
+        us = _time_calls(fn, calls, None, stream)
+        pos = np.searchsorted(k, qh)
+        hit = (pos < k.size) & (k[np.minimum(pos, k.size - 1)] == qh)
+        ok = bool(np.array_equal(of.cpu().numpy().astype(bool), hit) and
+                  np.array_equal(ov.cpu().numpy()[hit], v[pos[hit]]))
+        return {"lookups_per_s": B / (statistics.fmean(us) / 1e6), "p50_us": us[len(us) // 2],
+                "p99_us": us[min(len(us) - 1, int(0.99 * len(us)))], "correct": ok}
+
+    out = {"batch_sweep": {"workload": f"{keys.size} uniform uint64 keys, fanout {a.fanout}, 90% hits"},
+           "tree_sweep": {"workload": "uniform uint64 keys, fanout 32, batch 1024 uniform queries, 90% hits"}}
+    for dist, z in (("uniform", None), ("zipf1.1", 1.1)):
+        row = {}
+        for B in (1, 16, 64, 256, 1024, 1 << 20):
+            row[f"b{B}"] = run(tree, keys, vals, B, z, W.SEED_BASE + 20 + B, 30 if B > 4096 else 300)
+        out["batch_sweep"][dist] = row
+    for n in (10, 1000, 100_000, 1_000_000, 20_000_000):
+        k = W.uniform_keys(n, 64, seed=W.SEED_BASE + 30 + n)
+        v = W.rank_values(n, 64)
+        t = bt.BTree(k, v, 32)
+        out["tree_sweep"][f"n{n}"] = run(t, k, v, 1024, None, W.SEED_BASE + 31, 300) | {"height": t.height}
+        t.close()
+    return out
 
 
 # ------------------------------------------------------ batching leg
@@ -911,6 +955,8 @@ def run_ours(a):
                             "lookups_per_s": b / (statistics.fmean(us) / 1e6)}
         line["small_batch_latency"] = lat
 
+    if not a.no_extras and not a.no_sweeps:
+        line["sweeps"] = sweep_leg(a, bt, stream, keys, vals, tree)
     if not a.no_extras and not a.no_paper_keys:
         line["paper_keys"] = paper_keys_leg(a, bt, flush, stream, peak)
     if not a.no_extras and not a.no_learned:
