@@ -51,6 +51,26 @@ def _draw_uniform(g: np.random.Generator, size: int, width_bits: int) -> np.ndar
     return g.integers(0, 2**32, size=size, dtype=np.uint64, endpoint=False)
 
 
+def _sorted_unique(a: np.ndarray) -> np.ndarray:
+    """np.unique(a) for a 1-D array, by sorting (the same result, without
+    numpy's hash-based path, which is slow for tens of millions of keys)."""
+    a = np.sort(a)
+    if a.size < 2:
+        return a
+    keep = np.empty(a.size, bool)
+    keep[0] = True
+    np.not_equal(a[1:], a[:-1], out=keep[1:])
+    return a[keep]
+
+
+def _in_sorted(values: np.ndarray, sorted_keys: np.ndarray) -> np.ndarray:
+    """np.isin(values, sorted_keys) for an ascending key array, by binary search."""
+    if sorted_keys.size == 0:
+        return np.zeros(values.size, bool)
+    pos = np.searchsorted(sorted_keys, values)
+    return sorted_keys[np.minimum(pos, sorted_keys.size - 1)] == values
+
+
 def _exactly_n(pool: np.ndarray, n: int, g: np.random.Generator) -> np.ndarray:
     if pool.size > n:
         keep = g.choice(pool.size, size=n, replace=False)
@@ -66,7 +86,7 @@ def uniform_keys(n: int, width_bits: int, seed: int) -> np.ndarray:
     pool = np.empty(0, np.uint64)
     while pool.size < n:
         need = n - pool.size
-        pool = np.unique(np.concatenate([pool, _draw_uniform(g, need + need // 16 + 16, width_bits)]))
+        pool = _sorted_unique(np.concatenate([pool, _draw_uniform(g, need + need // 16 + 16, width_bits)]))
     return _exactly_n(pool, n, g).astype(key_dtype(width_bits))
 
 
@@ -84,7 +104,7 @@ def lognormal_mixture_keys(n: int, seed: int, mus=(0.0, 1.0, 2.0), sigmas=(1.0, 
         comp = g.integers(0, mus.size, size=size)
         x = g.lognormal(mean=mus[comp], sigma=sigmas[comp])
         k = np.floor(np.minimum(x * scale, limit)).astype(np.uint64)
-        pool = np.unique(np.concatenate([pool, k]))
+        pool = _sorted_unique(np.concatenate([pool, k]))
     return _exactly_n(pool, n, g)
 
 
@@ -139,9 +159,11 @@ def make_queries(keys: np.ndarray, nq: int, hit_frac: float, seed: int, width_bi
     if nm:
         miss = np.empty(0, np.uint64)
         ku = keys.astype(np.uint64)
+        if ku.size > 1 and not np.all(ku[1:] >= ku[:-1]):
+            ku = np.sort(ku)
         while miss.size < nm:
             d = _draw_uniform(g, (nm - miss.size) + 16, width_bits)
-            d = d[~np.isin(d, ku)]
+            d = d[~_in_sorted(d, ku)]
             miss = np.concatenate([miss, d])
         out[~is_hit] = miss[:nm]
     return out.astype(dt)
