@@ -4,16 +4,17 @@
  * The library answers batches of point queries against a static B+ tree by
  * the level-wise batch traversal of Tzschoppe et al., "Efficient Batch Search
  * Algorithm for B+ Tree Index Structures with Level-Wise Traversal on FPGAs":
- * the batch is sorted (Sec. IV-A), then descends the tree one level at a time;
+ * the batch is sorted (Sec. IV-A; here partitioned by approximate key rank,
+ * see bt_sort_batch), then descends the tree one level at a time;
  * every node needed at a level is fetched once per group of queries routed to
  * it and compared against all of them (Sec. IV-A, Sec. IV-F); a query goes to
  * the first slot whose separator it is less than or equal to (Sec. IV-E); at
  * the leaf an equal key yields its data, otherwise -1 (Sec. IV-D).
  *
  * Conventions for every call:
- *   - Keys and values are unsigned integers of 4 or 8 bytes, compared as
- *     unsigned integers (the paper's 32-byte keys compared byte by byte,
- *     Sec. IV-E, are replaced by native integer compares).
+ *   - Keys are unsigned integers of 4 or 8 bytes, compared as unsigned
+ *     integers, or the paper's 32-byte keys compared byte by byte (Sec. IV-E;
+ *     BT_B32).  Values are unsigned integers of 4 or 8 bytes.
  *   - "d_" pointers are device (GPU global memory) pointers owned by the
  *     caller; "h_" pointers are host pointers owned by the caller.  Nothing the
  *     caller passes is freed or retained after a call returns, except that a
@@ -41,11 +42,10 @@ extern "C" {
 struct CUstream_st;
 typedef struct CUstream_st *bt_stream;
 
-/* Width of keys and values in bytes. */
-/* Key and value widths.  BT_B32 (keys only) is the paper's 32-byte key
+/* Key and value widths in bytes.  BT_B32 (keys only) is the paper's 32-byte key
  * (Sec. IV-B, IV-E): a string of 32 bytes compared byte by byte from the
  * first, the first unequal byte deciding (lexicographic order, as memcmp);
- * key arrays and query arrays hold 32 bytes per key. */
+ * key arrays and query arrays hold 32 bytes per key, as they are. */
 typedef enum bt_width { BT_U32 = 4, BT_U64 = 8, BT_B32 = 32 } bt_width;
 
 typedef enum bt_status {
@@ -72,7 +72,7 @@ typedef struct bt_model bt_model;
 typedef struct bt_info {
     uint32_t height;                       /* number of levels; 0 for an empty tree */
     uint32_t fanout;                       /* m: max children of an inner node */
-    uint32_t key_bytes;                    /* 4 or 8 */
+    uint32_t key_bytes;                    /* 4, 8 or 32 */
     uint32_t val_bytes;                    /* 4 or 8 */
     uint64_t n;                            /* keys stored */
     uint64_t level_nodes[BT_MAX_LEVELS];   /* nodes per level */
@@ -145,8 +145,8 @@ bt_status bt_tree_info(const bt_tree *tree, bt_info *out);
 bt_status bt_tree_copy_image(const bt_tree *tree, void *h_dst, uint64_t bytes);
 
 /* Bytes of device workspace bt_search_batch needs for a batch of nq queries
- * (sort buffers and radix histograms).  Depends only on the tree's key width
- * and nq. */
+ * (the partitioned batch and the partition's bucket totals).  Depends only on
+ * the tree's key width and nq. */
 uint64_t bt_search_workspace_bytes(const bt_tree *tree, uint64_t nq);
 
 /* Options for bt_search_batch_ex. */
@@ -202,10 +202,12 @@ bt_status bt_search_batch_ex(const bt_tree *tree, const void *d_queries, uint64_
  * buckets, at most 2^13; 0 = no reordering: the queries are copied and the
  * index is the identity):
  *   bucket(q) = (c << r) | s, where c = the number of the tree's splitters
- *   (bt_info.nsplit keys, see bt_build) smaller than q and s = floor(2^r *
- *   (q - lo) / (hi - lo + 1)) in fp32 over the splitter segment (lo, hi]
- *   holding q, clamped to [0, 2^r - 1]; r = sort_bits - bitlen(nsplit)
- *   when positive, else bucket = c >> (bitlen(nsplit) - sort_bits).
+ *   (bt_info.nsplit keys, see bt_build) smaller than q, and s = the fp32
+ *   product (q - lo) * inv_c * 2^r truncated and clamped to [0, 2^r - 1],
+ *   with (lo, hi] the splitter segment holding q and inv_c its stored
+ *   reciprocal width (32-byte keys: q - lo over the 8 bytes after the
+ *   segment's shared prefix); r = sort_bits - bitlen(nsplit) when positive,
+ *   else bucket = c >> (bitlen(nsplit) - sort_bits).
  * The order of queries with equal buckets is unspecified (it follows the
  * order of device atomics and may differ between calls).
  *
@@ -275,7 +277,7 @@ bt_status bt_search_batch_host(const bt_tree *tree, const void *h_queries, uint6
  * critical request path that must not call cudaMalloc/cudaFree (they can
  * synchronize the whole device).
  *
- * Scratch space (sort buffers, histograms, bucket cursors) is a 2 MiB
+ * Scratch space (the partitioned batch and the bucket totals) is a 2 MiB
  * file-scope device array inside the library; every GPU that loads the
  * library holds it until the process exits.  The caller still passes the
  * queries and the outputs, as for bt_search_batch.
@@ -291,7 +293,9 @@ bt_status bt_search_batch_host(const bt_tree *tree, const void *h_queries, uint6
  * and it keeps the last call's contents (each search clears what must start
  * at zero), so calls whose work overlaps on the GPU -- on different streams,
  * or from different threads -- race and must be serialised by the caller.
- * Errors: as bt_search_batch, plus BT_ERR_ARG for nq > BT_NOALLOC_MAX_QUERIES.
+ * Errors: as bt_search_batch, plus BT_ERR_ARG for nq > BT_NOALLOC_MAX_QUERIES
+ * and BT_ERR_WORKSPACE when the batch's scratch exceeds the array (32-byte
+ * keys: above about 57,000 queries).
  */
 #define BT_NOALLOC_MAX_QUERIES 65536
 bt_status bt_search_batch_noalloc(const bt_tree *tree, const void *d_queries, uint64_t nq,
