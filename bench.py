@@ -141,6 +141,21 @@ def touched(keys: np.ndarray, level_nodes: list[int], m: int, q: np.ndarray, val
     return counts, int(sectors)
 
 
+def rank_touched(n: int, level_nodes: list[int], m: int, rank: np.ndarray, hit: np.ndarray, val_bytes: int):
+    """touched() for queries given by their lower-bound rank among the n sorted
+    keys (any key type): a query goes to the first node whose largest key has
+    rank >= its own, since q <= key[r] exactly when lower_bound(q) <= r.
+    Returns the distinct nodes per level and the distinct 32-byte value
+    sectors read by the hits."""
+    node_max_rank = [x.astype(np.int64) for x in level_node_max(np.arange(n, dtype=np.uint64), level_nodes)]
+    counts = [int(np.unique(np.minimum(np.searchsorted(mr, rank), mr.size - 1)).size) for mr in node_max_rank]
+    leaf = np.minimum(np.searchsorted(node_max_rank[-1], rank), node_max_rank[-1].size - 1)
+    first = np.concatenate([[0], node_max_rank[-1][:-1] + 1])
+    slot = rank - first[leaf]
+    sect = int(np.unique(((leaf[hit] * m + slot[hit]) * val_bytes) // 32).size)
+    return counts, sect
+
+
 def descend_algorithmic_bytes(counts, sectors, m, kb, vb, B) -> int:
     """Bytes the descent must move at least: every distinct node's key block
     once, every distinct value sector once, the sorted queries and their
@@ -412,8 +427,6 @@ def paper_keys_leg(a, bt, flush, stream, peak):
     tree = bt.BTree(keys, vals, m)
     res = {"workload": f"{n} distinct 32-byte keys (uniform random bytes), 8-byte values, fanout {m}, "
                        "90% hits, uniform queries"}
-    # the largest key under every node, as a key rank, per level (even bulk load)
-    node_max_rank = [x.astype(np.int64) for x in level_node_max(np.arange(n, dtype=np.uint64), tree.level_nodes)]
     for B, steps in ((1000, 300), (1 << 20, 50)):
         qh = W.make_byte_queries(keys, B, 0.9, seed=W.SEED_BASE + 9 + B)
         q = torch.from_numpy(qh).cuda()
@@ -440,12 +453,7 @@ def paper_keys_leg(a, bt, flush, stream, peak):
             bt.bt_sort_batch(tree.handle, q, B, -1, sq, si, ws, nb, stream)
             dfn = lambda: bt.bt_descend_sorted(tree.handle, sq, si, B, v, f, None, stream)
             dus = _time_calls(dfn, steps, flush, stream)
-            counts = [int(np.unique(np.minimum(np.searchsorted(mr, rank), mr.size - 1)).size)
-                      for mr in node_max_rank]
-            leaf = np.minimum(np.searchsorted(node_max_rank[-1], rank), node_max_rank[-1].size - 1)
-            first = np.concatenate([[0], node_max_rank[-1][:-1] + 1])
-            slot = rank - first[leaf]
-            sect = np.unique(((leaf[hit] * m + slot[hit]) * 8) // 32).size
+            counts, sect = rank_touched(n, tree.level_nodes, m, rank, hit, 8)
             alg = descend_algorithmic_bytes(counts, int(sect), m, 32, 8, B)
             d_mean = statistics.fmean(dus)
             row["descend_us"] = d_mean

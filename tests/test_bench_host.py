@@ -26,6 +26,28 @@ def test_touched_counts_match_oracle(m, n, nq, zipf):
     assert counts == oc and sectors == osec
 
 
+@pytest.mark.parametrize("m,n,prefix", [(16, 5000, 0), (8, 30000, 4), (32, 100000, 24)])
+def test_rank_touched_matches_byte_oracle(m, n, prefix):
+    """Routing by lower-bound rank gives the byte-key oracle's distinct nodes
+    per level and the distinct value sectors of its hits (leaf, slot)."""
+    from oracle.bytes_keys import OracleBytesTree
+    keys = W.byte_keys(n, 32, seed=60 + n, prefix_bytes=prefix)
+    vals = np.arange(n, dtype=np.uint64)
+    o = OracleBytesTree(keys, vals, m)
+    q = W.make_byte_queries(keys, 4000, 0.7, seed=61)
+    kv = keys.view("V32").ravel()
+    rank = np.searchsorted(kv, q.view("V32").ravel())
+    hit = rank < n
+    hit[hit] = kv[rank[hit]] == q.view("V32").ravel()[hit]
+    counts, sect = bench.rank_touched(n, o.level_nodes(), m, rank, hit, 8)
+    paths = o.paths(q)
+    assert counts == [int(np.unique(paths[:, l]).size) for l in range(paths.shape[1])]
+    _, found, leaf, slot = o.search(q)
+    assert np.array_equal(found.astype(bool), hit)
+    h = found == 1
+    assert sect == np.unique(((leaf[h] * m + slot[h].astype(np.uint64)) * 8) // 32).size
+
+
 def test_iqm_eq2_hand_values():
     # n = 8: drop the lowest and highest two, mean of the middle four
     assert bench.iqm([8, 1, 7, 2, 6, 3, 5, 4]) == 4.5
