@@ -87,6 +87,16 @@ def workload_name(a) -> str:
             f"uint64 values, batch {a.batch}, {int(round(a.hit * 100))}% hits, {dist} queries")
 
 
+def workload_config(a, world: int) -> dict:
+    """The workload both arms run (the same dict in both JSON lines)."""
+    return {"workload": workload_name(a), "keys": a.keys, "fanout": a.fanout, "batch": a.batch,
+            "hit_frac": a.hit, "query_dist": "uniform" if a.zipf is None else f"zipf{a.zipf}",
+            "l2": ("GPU arm: not flushed between steps (the 282 MB tree exceeds the 129 MB L2; batches "
+                   "rotate); a 256 MB write-flushed loop is reported beside it" if a.l2 == "none" else
+                   f"GPU arm: L2 {a.l2}-flushed (256 MB) before every timed step"),
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
 def make_tree_data(a):
     keys = W.uniform_keys(a.keys, 64, seed=W.SEED_BASE + 2)
     vals = W.rank_values(a.keys, 64)
@@ -818,14 +828,13 @@ def run_ours(a):
         "warmup": a.warmup, "ms_per_step": statistics.fmean(step_ms), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64",
         "data": "synthetic (seeded uniform keys and query mix)",
-        "config": {"workload": workload_name(a), "keys": a.keys, "fanout": m, "batch": B,
-                   "hit_frac": a.hit, "query_dist": "uniform" if a.zipf is None else f"zipf{a.zipf}",
-                   "sort_bits": "auto" if sort_bits < 0 else sort_bits,
+        "config": workload_config(a, world),
+        "launch": {"sort_bits": "auto" if sort_bits < 0 else sort_bits,
                    "staging": "bulk" if a.staging == 1 else "cp.async", "lane_queries": a.lane_queries,
                    "l2": {"write": "flushed before every timed step (256 MB device write)",
                           "read": "flushed before every timed step (256 MB device read)",
-                          "none": "not flushed: the 282 MB tree exceeds the 129 MB L2"}[a.l2],
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+                          "none": "not flushed: the 282 MB tree exceeds the 129 MB L2 and 4 batches "
+                                  "rotate"}[a.l2]},
         "p50_us": 1e3 * sdev[len(sdev) // 2], "p99_us": 1e3 * sdev[min(len(sdev) - 1, int(0.99 * len(sdev)))],
         "iqm_us": 1e3 * iqm(step_ms),
         "phase_ms": {"sort": statistics.fmean(sort_ms), "descend": statistics.fmean(desc_ms)},
@@ -1014,8 +1023,7 @@ def run_reference(a):
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * total / a.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
         "data": "synthetic (seeded uniform keys and query mix)",
-        "config": {"workload": workload_name(a), "keys": a.keys, "fanout": a.fanout, "batch": a.batch,
-                   "hit_frac": a.hit, "query_dist": "uniform" if a.zipf is None else f"zipf{a.zipf}"},
+        "config": workload_config(a, world),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"each step: the first {sample} queries of the batch, split evenly "
                                    f"over {cores} threads"},
