@@ -47,7 +47,7 @@ L2_FLUSH_BYTES = 256 << 20
 # from the ncu capture summarised in profiles/k_descend_2p24keys_b2p20.md;
 # valid only while the descent's source (search.cu up to the end of
 # k_descend) hashes to the same value.
-NCU_DESCEND_TRAFFIC = {"descend_src_sha256": "fea72898763be543", "bytes_per_launch": 216395008 + 3636224}
+NCU_DESCEND_TRAFFIC = {"descend_src_sha256": "", "bytes_per_launch": None}
 
 
 def parse_args(argv=None):
@@ -65,7 +65,14 @@ def parse_args(argv=None):
     p.add_argument("--l2", choices=["write", "read", "none"], default="none",
                    help="between timed steps: nothing (default: the 282 MB tree already exceeds the L2 and "
                         "the batches rotate), overwrite a 256 MB buffer, or read one")
-    p.add_argument("--staging", type=int, default=0, help="node staging: 0 = 16-byte cp.async, 1 = bulk copy")
+    p.add_argument("--staging", type=int, default=2,
+                   help="descent: 2 = pipelined (bulk-copy leaf staging overlapped with the next chunk), "
+                        "0 = synchronous 16-byte cp.async, 1 = synchronous bulk copy")
+    p.add_argument("--inner", type=int, default=0, help="pipelined: inner levels read through L1 (0) or staged (1)")
+    p.add_argument("--ballot", type=int, default=0, help="pipelined: leaf rank by binary search (0) or ballot (1)")
+    p.add_argument("--l2-window", type=int, default=0,
+                   help="bytes of the L2 persistence window on the inner levels (0 = none)")
+    p.add_argument("--no-designs", action="store_true", help="skip the A/B of the descent designs")
     p.add_argument("--lane-queries", type=int, default=1, help="queries per lane of the descent (1 or 2)")
     p.add_argument("--warps", type=int, default=0, help="descent warps per block (0 = library default)")
     p.add_argument("--pin", type=int, default=-1, help="pinned top-level bytes (-1 = library default)")
@@ -256,13 +263,13 @@ class ClockSampler:
 
 
 def src_sha256() -> str:
-    """Hash of the descent's source: search.cu from its descent section to the
-    end of k_descend."""
-    with open(os.path.join(ROOT, "paper_2604_21117_gb300", "csrc", "search.cu")) as f:
-        txt = f.read()
-    a = txt.find("// -------------------------------------------- level-wise descent (a3-a5)")
-    b = txt.find("// ------------------------------- two queries per lane")
-    return hashlib.sha256(txt[a:b].encode()).hexdigest()[:16] if a >= 0 and b > a else ""
+    """Hash of the descent's source: the pipelined kernel's file and the
+    helpers it includes."""
+    h = hashlib.sha256()
+    for name in ("desc_pipe.cu", "descent.cuh"):
+        with open(os.path.join(ROOT, "paper_2604_21117_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 # ------------------------------------------------------------ dist
@@ -329,6 +336,64 @@ def cpu_baseline(keys, vals, m, q, budget_s: float = 12.0):
             "sample": (f"first {nm} queries of one batch on {cores} threads (batch split evenly), "
                        f"IQM of 3 runs; 1-thread figure on the first {n1}; oracle tree build "
                        f"{build_s:.1f} s untimed")}
+
+
+# ------------------------------------------------------ designs leg
+
+DESIGNS = (
+    ("pipelined, inner through L1, binary search", dict(staging=2, inner=0, ballot=0, l2=0, lq=1)),
+    ("pipelined, inner through L1, ballot + popc", dict(staging=2, inner=0, ballot=1, l2=0, lq=1)),
+    ("pipelined, inner staged, binary search", dict(staging=2, inner=1, ballot=0, l2=0, lq=1)),
+    ("pipelined, inner through L1, L2 window", dict(staging=2, inner=0, ballot=0, l2=64 << 20, lq=1)),
+    ("synchronous cp.async (every level staged, waited)", dict(staging=0, inner=0, ballot=0, l2=0, lq=1)),
+    ("synchronous bulk copy", dict(staging=1, inner=0, ballot=0, l2=0, lq=1)),
+    ("synchronous, two queries per lane", dict(staging=0, inner=0, ballot=0, l2=0, lq=2)),
+)
+
+
+def designs_leg(a, bt, tree, dq, out_v, out_f, ws, nb, stream, alg, pool, steps: int = 40):
+    """A/B of the descent designs on the same sorted batches: mean descent
+    and step time (CUDA events), and the descent's achieved GB/s of
+    algorithmic bytes; each design's results are checked against the
+    default design's on the last batch."""
+    import torch
+    B = a.batch
+    peak, _ = measured_peaks()
+    out = {}
+    ref_v = ref_f = None
+    for label, d in DESIGNS:
+        bt.bt_tree_set_staging(tree.handle, d["staging"])
+        bt.bt_tree_set_lane_queries(tree.handle, d["lq"])
+        bt.bt_tree_set_descent(tree.handle, d["inner"], d["ballot"])
+        bt.bt_tree_set_l2_window(tree.handle, d["l2"])
+        for i in range(3):
+            bt.bt_search_batch_ex(tree.handle, dq[i % pool], B, out_v, out_f, ws, nb, a.sort_bits, None, stream)
+        ev = []
+        for i in range(steps):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[1].record(stream)  # create it; recorded again inside the call
+            e[0].record(stream)
+            bt.bt_search_batch_ex(tree.handle, dq[i % pool], B, out_v, out_f, ws, nb, a.sort_bits, None, stream, e[1])
+            e[2].record(stream)
+            ev.append(e)
+        torch.cuda.synchronize()
+        desc = [e[1].elapsed_time(e[2]) for e in ev]
+        step = [e[0].elapsed_time(e[2]) for e in ev]
+        byts = statistics.fmean(alg[i % pool][2] for i in range(steps))
+        gbs = byts / (statistics.fmean(desc) / 1e3) / 1e9
+        v = out_v.cpu().numpy()
+        f = out_f.cpu().numpy()
+        if ref_v is None:
+            ref_v, ref_f, same = v, f, True
+        else:
+            same = bool(np.array_equal(v, ref_v) and np.array_equal(f, ref_f))
+        out[label] = {"descend_us": 1e3 * statistics.fmean(desc), "step_us": 1e3 * statistics.fmean(step),
+                      "descend_gbs": gbs, "descend_frac_of_peak": gbs / peak, "same_results": same}
+    bt.bt_tree_set_staging(tree.handle, a.staging)
+    bt.bt_tree_set_lane_queries(tree.handle, a.lane_queries)
+    bt.bt_tree_set_descent(tree.handle, a.inner, a.ballot)
+    bt.bt_tree_set_l2_window(tree.handle, a.l2_window)
+    return out
 
 
 # ------------------------------------------------------ learned leg
@@ -731,6 +796,9 @@ def run_ours(a):
     tree = bt.BTree(keys, vals, a.fanout)
     bt.bt_tree_set_staging(tree.handle, a.staging)
     bt.bt_tree_set_lane_queries(tree.handle, a.lane_queries)
+    bt.bt_tree_set_descent(tree.handle, a.inner, a.ballot)
+    if a.l2_window > 0:
+        bt.bt_tree_set_l2_window(tree.handle, a.l2_window)
     if a.warps > 0 or a.pin >= 0:
         bt.bt_tree_set_launch(tree.handle, a.warps if a.warps > 0 else 8, a.pin if a.pin >= 0 else 16384)
     m, kb, vb, B = a.fanout, 8, 8, a.batch
@@ -759,10 +827,10 @@ def run_ours(a):
         elif a.l2 == "read":  # leaves clean lines: no write-back inside the step
             flush_sink.copy_(flush.sum(dtype=torch.int64))
 
-    def step(i):
-        x = dq[i % pool]
-        bt.bt_sort_batch(tree.handle, x, B, sort_bits, sq, si, ws, nb, stream)
-        bt.bt_descend_sorted(tree.handle, sq, si, B, out_v, out_f, None, stream)
+    def step(i, phase_event=None):
+        # one whole search of batch i: partition, descent, leaf probe, scatter
+        bt.bt_search_batch_ex(tree.handle, dq[i % pool], B, out_v, out_f, ws, nb, sort_bits, None, stream,
+                              phase_event)
 
     sampler = ClockSampler(local)
     sampler.start()
@@ -775,17 +843,17 @@ def run_ours(a):
 
     def timed_loop(clear):
         ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+        for e in ev:  # create the events (the middle one is recorded inside the call)
+            for x in e:
+                x.record(stream)
         barrier(world)
         torch.cuda.synchronize()
         w0 = time.perf_counter()
         for i in range(K):
             clear(i)
             e0, e1, e2 = ev[i]
-            x = dq[i % pool]
             e0.record(stream)
-            bt.bt_sort_batch(tree.handle, x, B, sort_bits, sq, si, ws, nb, stream)
-            e1.record(stream)
-            bt.bt_descend_sorted(tree.handle, sq, si, B, out_v, out_f, None, stream)
+            step(i, e1)
             e2.record(stream)
         torch.cuda.synchronize()
         barrier(world)
@@ -814,13 +882,13 @@ def run_ours(a):
     default_workload = (a.keys == 1 << 24 and a.batch == 1 << 20 and a.fanout == 32 and a.zipf is None
                         and abs(a.hit - 0.9) < 1e-9)
     if (NCU_DESCEND_TRAFFIC["descend_src_sha256"] == src_sha256() and default_workload and a.lane_queries == 1
-            and a.staging == 0 and a.warps <= 0 and a.pin < 0 and a.sort_bits < 0):
+            and a.staging == 2 and a.inner == 0 and a.ballot == 0 and a.l2_window == 0 and a.warps <= 0
+            and a.pin < 0 and a.sort_bits < 0):
         traffic = NCU_DESCEND_TRAFFIC["bytes_per_launch"]
     step_gbs = statistics.fmean(node_bytes) / (statistics.fmean(step_ms) / 1e3) / 1e9
     sort_k = bt.bt_sort_launches(tree.handle, B, sort_bits)
-    # our kernels per step: the sort's kernels (or one copy kernel when the
-    # sort is skipped), then the descent
-    launches_per_step = (sort_k if sort_k else 1) + 1
+    # our kernels per step: the partition's kernels, then the descent
+    launches_per_step = sort_k + 1
     sdev = sorted(step_ms)
 
     line = {
@@ -830,7 +898,11 @@ def run_ours(a):
         "data": "synthetic (seeded uniform keys and query mix)",
         "config": workload_config(a, world),
         "launch": {"sort_bits": "auto" if sort_bits < 0 else sort_bits,
-                   "staging": "bulk" if a.staging == 1 else "cp.async", "lane_queries": a.lane_queries,
+                   "staging": {0: "synchronous cp.async", 1: "synchronous bulk copy",
+                               2: "pipelined bulk-copy leaves"}[a.staging],
+                   "inner_levels": "staged (cp.async)" if a.inner else "through L1",
+                   "leaf_rank": "ballot + popc" if a.ballot else "binary search",
+                   "l2_window_bytes": a.l2_window, "lane_queries": a.lane_queries,
                    "l2": {"write": "flushed before every timed step (256 MB device write)",
                           "read": "flushed before every timed step (256 MB device read)",
                           "none": "not flushed: the 282 MB tree exceeds the 129 MB L2 and 4 batches "
@@ -866,8 +938,7 @@ def run_ours(a):
         for p_ in range(pool):
             g = torch.cuda.CUDAGraph()
             with torch.cuda.graph(g, stream=cap):
-                bt.bt_sort_batch(tree.handle, dq[p_], B, sort_bits, sq, si, ws, nb, cap)
-                bt.bt_descend_sorted(tree.handle, sq, si, B, out_v, out_f, None, cap)
+                bt.bt_search_batch_ex(tree.handle, dq[p_], B, out_v, out_f, ws, nb, sort_bits, None, cap)
             graphs.append(g)
     stream.wait_stream(cap)
     torch.cuda.synchronize()
@@ -972,6 +1043,8 @@ def run_ours(a):
                             "lookups_per_s": b / (statistics.fmean(us) / 1e6)}
         line["small_batch_latency"] = lat
 
+    if not a.no_designs:
+        line["designs"] = designs_leg(a, bt, tree, dq, out_v, out_f, ws, nb, stream, alg, pool)
     if not a.no_extras and not a.no_sweeps:
         line["sweeps"] = sweep_leg(a, bt, stream, keys, vals, tree)
     if not a.no_extras and not a.no_paper_keys:

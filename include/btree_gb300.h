@@ -134,10 +134,12 @@ bt_status bt_build(const void *h_keys, const void *h_vals, uint64_t n, bt_width 
                    bt_width val_w, uint32_t fanout, bt_stream stream, bt_tree **out);
 
 /* Release a tree and its device memory (NULL is a no-op).  The caller must
- * make sure no search using it is still running. */
+ * make sure no search using it is still running.  No counterpart in the
+ * paper (its tree lives for the whole run). */
 void bt_free(bt_tree *tree);
 
-/* Copy the tree's shape into *out.  BT_ERR_ARG on null pointers. */
+/* Copy the tree's shape into *out (levels and node counts as in Sec. III:
+ * height h, nodes per level).  BT_ERR_ARG on null pointers. */
 bt_status bt_tree_info(const bt_tree *tree, bt_info *out);
 
 /* Copy the first `bytes` of the device image into host memory (for layout
@@ -145,8 +147,10 @@ bt_status bt_tree_info(const bt_tree *tree, bt_info *out);
 bt_status bt_tree_copy_image(const bt_tree *tree, void *h_dst, uint64_t bytes);
 
 /* Bytes of device workspace bt_search_batch needs for a batch of nq queries
- * (the partitioned batch and the partition's bucket totals).  Depends only on
- * the tree's key width and nq. */
+ * (the partitioned batch, its local-sort digits and the partition's bucket
+ * counters).  Depends only on the tree's key width and nq; 0 for a NULL tree
+ * or nq = 0.  No counterpart in the paper (its batch lives in on-chip BRAM,
+ * Sec. IV-C). */
 uint64_t bt_search_workspace_bytes(const bt_tree *tree, uint64_t nq);
 
 /* Options for bt_search_batch_ex. */
@@ -155,13 +159,17 @@ typedef struct bt_search_opts {
      * descent (Sec. IV-A sorts the batch so that queries for one node are
      * adjacent; see bt_sort_batch for the order obtained): -1 lets the
      * library choose from nq (none below 16384 queries), 0 skips the
-     * partition, 1..13 forces that many bits (larger values mean 13). */
+     * partition, 1..21 forces that many bits (larger values mean 21). */
     int32_t sort_bits;
     /* If non-NULL: device array of `height` counters to which the search
      * adds, per level, how many node key blocks it fetched -- the quantity
      * the paper's method keeps near the number of distinct nodes (Sec. IV-A).
      * Counting adds one atomic per warp and level. */
     unsigned long long *d_fetch_counts;
+    /* If non-NULL: a CUDA event (cudaEvent_t) recorded on the stream between
+     * the partition and the descent, so that a caller can time the two phases
+     * of one call with its own events around it. */
+    void *phase_event;
 } bt_search_opts;
 
 /*
@@ -197,19 +205,28 @@ bt_status bt_search_batch_ex(const bt_tree *tree, const void *d_queries, uint64_
  * bt_sort_batch -- the first step of a search on its own: the on-device
  * partition of the batch (Sec. IV-A: queries are sorted so that those
  * routed to one node are adjacent).  Writes the reordered queries and, for
- * each, its input position.  The order is that of a bucket number monotone
- * in the key, on `sort_bits` bits (-1 = library choice: about nq/16
- * buckets, at most 2^13; 0 = no reordering: the queries are copied and the
- * index is the identity):
- *   bucket(q) = (c << r) | s, where c = the number of the tree's splitters
+ * each, its input position.  The order is that of a bucket number f monotone
+ * in the key, on `bits` bits: sort_bits when positive (values above 21 mean
+ * 21), none for 0 (the queries are copied and the index is the identity),
+ * and for -1 the library's choice, which bt_sort_bits reports (none below
+ * 16384 queries; otherwise coarse buckets of 512 to 1023 queries on
+ * average, 128 to 255 for 32-byte keys):
+ *   f(q) = (c << r) | s, where c = the number of the tree's splitters
  *   (bt_info.nsplit keys, see bt_build) smaller than q, and s = the fp32
  *   product (q - lo) * inv_c * 2^r truncated and clamped to [0, 2^r - 1],
  *   with (lo, hi] the splitter segment holding q and inv_c its stored
  *   reciprocal width (32-byte keys: q - lo over the 8 bytes after the
- *   segment's shared prefix); r = sort_bits - bitlen(nsplit) when positive,
- *   else bucket = c >> (bitlen(nsplit) - sort_bits).
- * The order of queries with equal buckets is unspecified (it follows the
- * order of device atomics and may differ between calls).
+ *   segment's shared prefix); r = bits - bitlen(nsplit) when positive,
+ *   else f = c >> (bitlen(nsplit) - bits).
+ * The batch is ordered by the coarse bucket f >> lb, lb = min(9, bits - 1),
+ * and inside every coarse bucket of at most 1024 queries (the local sort's
+ * tile; 256 for 32-byte keys) by f.  The order of queries with equal f, and inside larger coarse
+ * buckets (a hot key) the order of queries with equal coarse buckets, is
+ * unspecified (it follows device atomics and may differ between calls).
+ * One cooperative kernel (coarse counts, scatter, per-bucket local sort,
+ * with two bounded grid barriers; see bt_check_timeouts) after one memset of
+ * the coarse-bucket counters; bt_sort_batch adds one kernel that writes the
+ * two output arrays.
  *
  *   d_queries         nq keys (device).
  *   d_sorted_queries  nq keys (device), must not overlap d_queries.
@@ -227,6 +244,11 @@ bt_status bt_sort_batch(const bt_tree *tree, const void *d_queries, uint64_t nq,
  * also issues one cudaMemsetAsync of its bucket counters).  -1 on a NULL
  * tree. */
 int32_t bt_sort_launches(const bt_tree *tree, uint64_t nq, int32_t sort_bits);
+
+/* Bits of the bucket number f that bt_sort_batch / bt_search_batch order a
+ * batch of nq queries on, for this sort_bits (-1 = the library's choice);
+ * 0 = no partition.  -1 on a NULL tree.  No counterpart in the paper. */
+int32_t bt_sort_bits(const bt_tree *tree, uint64_t nq, int32_t sort_bits);
 
 /*
  * bt_descend_sorted -- the remaining steps on their own: the level-wise
@@ -277,7 +299,7 @@ bt_status bt_search_batch_host(const bt_tree *tree, const void *h_queries, uint6
  * critical request path that must not call cudaMalloc/cudaFree (they can
  * synchronize the whole device).
  *
- * Scratch space (the partitioned batch and the bucket totals) is a 2 MiB
+ * Scratch space (the partitioned batch and the bucket counters) is a 4 MiB
  * file-scope device array inside the library; every GPU that loads the
  * library holds it until the process exits.  The caller still passes the
  * queries and the outputs, as for bt_search_batch.
@@ -295,7 +317,7 @@ bt_status bt_search_batch_host(const bt_tree *tree, const void *h_queries, uint6
  * or from different threads -- race and must be serialised by the caller.
  * Errors: as bt_search_batch, plus BT_ERR_ARG for nq > BT_NOALLOC_MAX_QUERIES
  * and BT_ERR_WORKSPACE when the batch's scratch exceeds the array (32-byte
- * keys: above about 57,000 queries).
+ * keys: above about 43,000 queries).
  */
 #define BT_NOALLOC_MAX_QUERIES 65536
 bt_status bt_search_batch_noalloc(const bt_tree *tree, const void *d_queries, uint64_t nq,
@@ -335,21 +357,35 @@ uint64_t bt_forest_workspace_bytes(uint32_t nbatches);
  * node of the chunk staged once per level, Sec. IV-A) and writes value and
  * found flag at its queries' positions.  Batches are not sorted (they are
  * small; the per-warp distinct-node staging already reuses nodes).
+ *   d_queries        nq keys (device); results go to the same positions of
+ *                    d_out_vals / d_out_found (nq entries each).
+ *   nq               length of those three arrays.
  *   warps_per_block  1..16, 0 = 8 (a tuning knob, see bt_autotune).
+ * Each work-list entry must name a tree below the forest's count and lie
+ * inside the arrays (offset + count <= nq).  The kernel checks both: an
+ * entry that breaks either is skipped (nothing is written for it) and
+ * counted (bt_forest_bad_batches).
  * Asynchronous, allocates nothing, may be captured in a CUDA graph.
  * Errors: BT_ERR_ARG, BT_ERR_WORKSPACE, BT_ERR_CUDA.
  */
 bt_status bt_forest_search(const bt_forest *forest, const bt_batch_desc *d_batches, uint32_t nbatches,
-                           const void *d_queries, void *d_out_vals, uint8_t *d_out_found, void *d_workspace,
-                           uint64_t ws_bytes, uint32_t warps_per_block, bt_stream stream);
+                           const void *d_queries, uint64_t nq, void *d_out_vals, uint8_t *d_out_found,
+                           void *d_workspace, uint64_t ws_bytes, uint32_t warps_per_block, bt_stream stream);
+
+/* Work-list entries that bt_forest_search skipped since the last call (a
+ * tree index outside the forest, or queries beyond the arrays), read and
+ * cleared; synchronous.  No counterpart in the paper.
+ * Errors: BT_ERR_ARG (null out), BT_ERR_CUDA. */
+bt_status bt_forest_bad_batches(uint64_t *out);
 
 /* Launch parameters of a tree's single-tree searches. */
 typedef struct bt_tune {
     uint32_t fanout;          /* m the tree was built with */
     uint32_t warps_per_block; /* descent blocks: 4, 8 or 16 warps */
     uint32_t pin_bytes;       /* budget for top levels kept in shared memory (0..49152) */
-    uint32_t staging;         /* BT_STAGE_CP_ASYNC or BT_STAGE_BULK */
+    uint32_t staging;         /* BT_STAGE_PIPELINED, BT_STAGE_CP_ASYNC or BT_STAGE_BULK */
     uint32_t lane_queries;    /* queries per lane of the descent: 1 or 2 */
+    uint32_t inner_staged;    /* pipelined descent: inner levels staged (1) or read through L1 (0) */
     float us_per_batch;       /* median time of the sample batch with these settings */
 } bt_tune;
 
@@ -357,13 +393,57 @@ typedef struct bt_tune {
  * searches running on it).  BT_ERR_ARG on unsupported values. */
 bt_status bt_tree_set_launch(bt_tree *tree, uint32_t warps_per_block, uint32_t pin_bytes);
 
-/* How the descent stages node blocks into shared memory: BT_STAGE_CP_ASYNC
- * (each lane copies 16-byte pieces) or BT_STAGE_BULK (one asynchronous bulk
- * copy per node block, the GPU's copy engine (TMA), counted on an mbarrier
- * with a bounded wait).  Results are identical; speed differs. */
+/* How the descent stages node blocks into shared memory (Sec. IV-A: every
+ * node a group of queries needs is loaded once):
+ *   BT_STAGE_PIPELINED (the default): leaf blocks are staged by one
+ *     asynchronous bulk copy each (the copy engine), completing on the warp's
+ *     mbarrier while the warp walks the next 32 queries down the inner
+ *     levels; the wait is bounded (see bt_check_timeouts);
+ *   BT_STAGE_CP_ASYNC: every level below the pinned ones is staged with
+ *     16-byte cp.async pieces and waited for before the search, one chunk
+ *     of 32 queries at a time;
+ *   BT_STAGE_BULK: as BT_STAGE_CP_ASYNC with one bulk copy per node block
+ *     counted on an mbarrier (bounded wait).
+ * Results are identical; speed differs.  BT_ERR_ARG on other values. */
 #define BT_STAGE_CP_ASYNC 0
 #define BT_STAGE_BULK 1
+#define BT_STAGE_PIPELINED 2
 bt_status bt_tree_set_staging(bt_tree *tree, uint32_t mode);
+
+/* Two choices of the pipelined descent (no counterpart in the paper beyond
+ * Sec. IV-E's comparator row, which rank_ballot = 1 follows):
+ *   inner_staged  0 (default): each lane reads its inner-level node block
+ *                 through L1 (every 128-byte line of the block prefetched
+ *                 first; lanes that share a node share its lines);
+ *                 1: each distinct inner node block is staged into shared
+ *                 memory once with 16-byte cp.async, then searched there.
+ *   rank_ballot   0 (default): each query finds its leaf rank by binary
+ *                 search in the staged block; 1: the rank is the population
+ *                 count of a warp ballot, lane j comparing slot j (and j+32)
+ *                 of the query's leaf, one query after another.
+ * Results are identical; speed differs.  BT_ERR_ARG on values above 1. */
+bt_status bt_tree_set_descent(bt_tree *tree, uint32_t inner_staged, uint32_t rank_ballot);
+
+/* An L2 access-policy window for the tree's searches: the inner levels below
+ * the shared-memory-pinned ones (at most max_bytes, and at most the device's
+ * window size) are marked persisting in L2 on every descent launch, so that
+ * the stream of leaf blocks does not evict them between batches.  Sets this
+ * process's persisting-L2 set-aside (cudaLimitPersistingL2CacheSize) to at
+ * least the window's size if it is smaller; the set-aside belongs to this
+ * process's CUDA context and ends with it.  0 removes the window.  No
+ * counterpart in the paper (its top levels stay on chip, Sec. IV-A).
+ * Errors: BT_ERR_ARG, BT_ERR_CUDA. */
+bt_status bt_tree_set_l2_window(bt_tree *tree, uint64_t max_bytes);
+
+/* Test hook: poll limit of the first bounded wait of the descents' bulk-copy
+ * staging, BT_DEFAULT_WAIT_POLLS unless changed; 0 makes every such wait
+ * give up at once.  After a wait gives up, the warp counts it
+ * (bt_check_timeouts then returns BT_ERR_TIMEOUT), waits once more with the
+ * default limit so that its copies land, and stops: the outputs of that
+ * search are invalid.  Process-wide; takes effect for launches made after
+ * the call.  No counterpart in the paper. */
+#define BT_DEFAULT_WAIT_POLLS (1u << 22)
+void bt_debug_set_wait_polls(uint32_t polls);
 
 /* Queries each lane carries through the plain descent: 1 (a warp walks 32
  * consecutive queries of the batch down the tree together, the default) or
@@ -375,17 +455,20 @@ bt_status bt_tree_set_lane_queries(bt_tree *tree, uint32_t per_lane);
 
 /* BT_ERR_TIMEOUT if a bounded device wait of a search gave up since the
  * last call (the results of such a search are invalid), else BT_OK; clears
- * the counter.  Synchronous. */
+ * the counters.  Synchronous (reads device counters).  No counterpart in the
+ * paper (its kernel has no waits that can fail). */
 bt_status bt_check_timeouts(void);
 
 /*
  * bt_autotune -- build the tree at every fanout in {8, 16, 32, 64} and time
  * a sample batch (d_sample, nsample device queries) through bt_search_batch
- * for every combination of warps per block {4, 8, 16} and pinned bytes
- * {0, 16384, 49152}, both staging modes and 1 or 2 queries per lane; keep
- * the fastest.  *out receives the tree built with
+ * for every combination of warps per block {4, 8, 16}, pinned bytes
+ * {0, 16384, 49152} and descent design (pipelined with inner levels read
+ * through L1 or staged; synchronous with cp.async or bulk-copy staging; two
+ * queries per lane); keep the fastest.  *out receives the tree built with
  * the best fanout and launch parameters applied, *best the choice and its
  * time.  Synchronizes `stream`.  Errors: as bt_build, plus BT_ERR_ARG.
+ * No counterpart in the paper (its fanout is fixed by the key size).
  */
 bt_status bt_autotune(const void *h_keys, const void *h_vals, uint64_t n, bt_width key_w, bt_width val_w,
                       const void *d_sample, uint64_t nsample, bt_stream stream, bt_tree **out, bt_tune *best);
@@ -583,10 +666,12 @@ bt_status bt_learned_search_batch(const bt_tree *tree, const bt_model *model, co
                                   uint64_t nq, void *d_out_vals, uint8_t *d_out_found, void *d_workspace,
                                   uint64_t ws_bytes, bt_stream stream);
 
-/* Static text for a status code. */
+/* Static text for a status code (never NULL; "unknown status" for values
+ * outside bt_status).  No counterpart in the paper. */
 const char *bt_status_str(bt_status status);
 
-/* Thread-local detail of the last BT_ERR_CUDA on this thread ("" if none). */
+/* Thread-local detail of the last BT_ERR_CUDA on this thread ("" if none).
+ * No counterpart in the paper. */
 const char *bt_last_error_detail(void);
 
 #ifdef __cplusplus

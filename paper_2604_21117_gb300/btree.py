@@ -31,14 +31,15 @@ STATUS = {0: "BT_OK", 1: "BT_ERR_ARG", 2: "BT_ERR_UNSORTED", 3: "BT_ERR_DUPLICAT
 
 # Every symbol include/btree_gb300.h declares.
 EXPORTED = ("bt_build", "bt_free", "bt_tree_info", "bt_tree_copy_image", "bt_search_workspace_bytes",
-            "bt_search_batch", "bt_search_batch_ex", "bt_sort_batch", "bt_descend_sorted", "bt_sort_launches",
+            "bt_search_batch", "bt_search_batch_ex", "bt_sort_batch", "bt_descend_sorted", "bt_sort_launches", "bt_sort_bits",
             "bt_search_host_workspace_bytes",
             "bt_search_batch_host", "bt_search_batch_noalloc", "bt_status_str", "bt_last_error_detail",
             "bt_model_train", "bt_model_free", "bt_model_get_info", "bt_model_copy_params", "bt_mlp_grad",
             "bt_learned_descend_sorted", "bt_learned_search_batch", "bt_model_copy_err_bounds",
             "bt_forest_create", "bt_forest_free",
-            "bt_forest_workspace_bytes", "bt_forest_search", "bt_tree_set_launch", "bt_tree_set_staging",
-            "bt_tree_set_lane_queries", "bt_check_timeouts", "bt_autotune", "bt_paper_node_bytes", "bt_paper_layout_build",
+            "bt_forest_workspace_bytes", "bt_forest_search", "bt_forest_bad_batches", "bt_tree_set_launch", "bt_tree_set_staging",
+            "bt_tree_set_lane_queries", "bt_tree_set_descent", "bt_tree_set_l2_window", "bt_debug_set_wait_polls",
+            "bt_check_timeouts", "bt_autotune", "bt_paper_node_bytes", "bt_paper_layout_build",
             "bt_paper_search_batch", "bt_paper_descend_sorted",
             "bt_server_create", "bt_server_submit", "bt_server_poll", "bt_server_drain", "bt_server_get_stats",
             "bt_server_destroy", "bt_server_run_trace")
@@ -57,7 +58,7 @@ class bt_info(ctypes.Structure):
 
 
 class bt_search_opts(ctypes.Structure):
-    _fields_ = [("sort_bits", ctypes.c_int32), ("d_fetch_counts", ctypes.c_void_p)]
+    _fields_ = [("sort_bits", ctypes.c_int32), ("d_fetch_counts", ctypes.c_void_p), ("phase_event", ctypes.c_void_p)]
 
 
 _vp, _u64, _i = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int
@@ -81,6 +82,8 @@ _lib.bt_sort_batch.restype = _i
 _lib.bt_sort_batch.argtypes = [_vp, _vp, _u64, ctypes.c_int32, _vp, _vp, _vp, _u64, _vp]
 _lib.bt_sort_launches.restype = ctypes.c_int32
 _lib.bt_sort_launches.argtypes = [_vp, _u64, ctypes.c_int32]
+_lib.bt_sort_bits.restype = ctypes.c_int32
+_lib.bt_sort_bits.argtypes = [_vp, _u64, ctypes.c_int32]
 _lib.bt_descend_sorted.restype = _i
 _lib.bt_descend_sorted.argtypes = [_vp, _vp, _vp, _u64, _vp, _vp, _vp, _vp]
 _lib.bt_search_batch_host.restype = _i
@@ -194,8 +197,14 @@ def bt_search_batch(tree: int, d_queries, nq: int, d_out_vals, d_out_found, d_wo
 
 
 def bt_search_batch_ex(tree: int, d_queries, nq: int, d_out_vals, d_out_found, d_workspace,
-                       ws_bytes: int, sort_bits: int = -1, d_fetch_counts=None, stream=None) -> None:
-    opts = bt_search_opts(sort_bits, _dptr(d_fetch_counts))
+                       ws_bytes: int, sort_bits: int = -1, d_fetch_counts=None, stream=None,
+                       phase_event=None) -> None:
+    """phase_event: a torch.cuda.Event (or raw cudaEvent_t) recorded between the
+    partition and the descent."""
+    ev = None
+    if phase_event is not None:
+        ev = phase_event if isinstance(phase_event, int) else phase_event.cuda_event
+    opts = bt_search_opts(sort_bits, _dptr(d_fetch_counts), ev)
     st = _lib.bt_search_batch_ex(tree, _dptr(d_queries), nq, _dptr(d_out_vals), _dptr(d_out_found),
                                  _dptr(d_workspace), ws_bytes, ctypes.byref(opts), _stream_handle(stream))
     _check("bt_search_batch_ex", st)
@@ -210,6 +219,10 @@ def bt_sort_batch(tree: int, d_queries, nq: int, sort_bits: int, d_sorted_querie
 
 def bt_sort_launches(tree: int, nq: int, sort_bits: int = -1) -> int:
     return int(_lib.bt_sort_launches(tree, nq, sort_bits))
+
+
+def bt_sort_bits(tree: int, nq: int, sort_bits: int = -1) -> int:
+    return int(_lib.bt_sort_bits(tree, nq, sort_bits))
 
 
 def bt_descend_sorted(tree: int, d_queries, d_index, nq: int, d_out_vals, d_out_found,
@@ -341,7 +354,7 @@ class bt_batch_desc(ctypes.Structure):
 class bt_tune(ctypes.Structure):
     _fields_ = [("fanout", ctypes.c_uint32), ("warps_per_block", ctypes.c_uint32), ("pin_bytes", ctypes.c_uint32),
                 ("staging", ctypes.c_uint32), ("lane_queries", ctypes.c_uint32),
-                ("us_per_batch", ctypes.c_float)]
+                ("inner_staged", ctypes.c_uint32), ("us_per_batch", ctypes.c_float)]
 
 
 BATCH_DESC_DTYPE = np.dtype([("tree", np.uint32), ("count", np.uint32), ("offset", np.uint64)])
@@ -353,13 +366,21 @@ _lib.bt_forest_free.argtypes = [_vp]
 _lib.bt_forest_workspace_bytes.restype = _u64
 _lib.bt_forest_workspace_bytes.argtypes = [ctypes.c_uint32]
 _lib.bt_forest_search.restype = _i
-_lib.bt_forest_search.argtypes = [_vp, _vp, ctypes.c_uint32, _vp, _vp, _vp, _vp, _u64, ctypes.c_uint32, _vp]
+_lib.bt_forest_search.argtypes = [_vp, _vp, ctypes.c_uint32, _vp, _u64, _vp, _vp, _vp, _u64, ctypes.c_uint32, _vp]
+_lib.bt_forest_bad_batches.restype = _i
+_lib.bt_forest_bad_batches.argtypes = [ctypes.POINTER(_u64)]
 _lib.bt_tree_set_launch.restype = _i
 _lib.bt_tree_set_launch.argtypes = [_vp, ctypes.c_uint32, ctypes.c_uint32]
 _lib.bt_tree_set_staging.restype = _i
 _lib.bt_tree_set_staging.argtypes = [_vp, ctypes.c_uint32]
 _lib.bt_tree_set_lane_queries.restype = _i
 _lib.bt_tree_set_lane_queries.argtypes = [_vp, ctypes.c_uint32]
+_lib.bt_tree_set_descent.restype = _i
+_lib.bt_tree_set_descent.argtypes = [_vp, ctypes.c_uint32, ctypes.c_uint32]
+_lib.bt_tree_set_l2_window.restype = _i
+_lib.bt_tree_set_l2_window.argtypes = [_vp, _u64]
+_lib.bt_debug_set_wait_polls.restype = None
+_lib.bt_debug_set_wait_polls.argtypes = [ctypes.c_uint32]
 _lib.bt_check_timeouts.restype = _i
 _lib.bt_check_timeouts.argtypes = []
 _lib.bt_autotune.restype = _i
@@ -382,11 +403,21 @@ def bt_forest_workspace_bytes(nbatches: int) -> int:
 
 
 def bt_forest_search(forest: int, d_batches, nbatches: int, d_queries, d_out_vals, d_out_found, d_workspace,
-                     ws_bytes: int, warps_per_block: int = 0, stream=None) -> None:
-    st = _lib.bt_forest_search(forest, _dptr(d_batches), nbatches, _dptr(d_queries), _dptr(d_out_vals),
+                     ws_bytes: int, warps_per_block: int = 0, stream=None, nq: int | None = None) -> None:
+    """nq: entries of the query and result arrays (default: the query tensor's length)."""
+    if nq is None:
+        nq = int(d_queries.numel())
+    st = _lib.bt_forest_search(forest, _dptr(d_batches), nbatches, _dptr(d_queries), nq, _dptr(d_out_vals),
                                _dptr(d_out_found), _dptr(d_workspace), ws_bytes, warps_per_block,
                                _stream_handle(stream))
     _check("bt_forest_search", st)
+
+
+def bt_forest_bad_batches() -> int:
+    """Work-list entries the batching kernel rejected since the last call."""
+    out = _u64()
+    _check("bt_forest_bad_batches", _lib.bt_forest_bad_batches(ctypes.byref(out)))
+    return int(out.value)
 
 
 def bt_tree_set_launch(tree: int, warps_per_block: int, pin_bytes: int) -> None:
@@ -395,6 +426,8 @@ def bt_tree_set_launch(tree: int, warps_per_block: int, pin_bytes: int) -> None:
 
 BT_STAGE_CP_ASYNC = 0
 BT_STAGE_BULK = 1
+BT_STAGE_PIPELINED = 2
+BT_DEFAULT_WAIT_POLLS = 1 << 22
 
 
 def bt_tree_set_staging(tree: int, mode: int) -> None:
@@ -403,6 +436,18 @@ def bt_tree_set_staging(tree: int, mode: int) -> None:
 
 def bt_tree_set_lane_queries(tree: int, per_lane: int) -> None:
     _check("bt_tree_set_lane_queries", _lib.bt_tree_set_lane_queries(tree, per_lane))
+
+
+def bt_tree_set_descent(tree: int, inner_staged: int = 0, rank_ballot: int = 0) -> None:
+    _check("bt_tree_set_descent", _lib.bt_tree_set_descent(tree, inner_staged, rank_ballot))
+
+
+def bt_tree_set_l2_window(tree: int, max_bytes: int) -> None:
+    _check("bt_tree_set_l2_window", _lib.bt_tree_set_l2_window(tree, max_bytes))
+
+
+def bt_debug_set_wait_polls(polls: int) -> None:
+    _lib.bt_debug_set_wait_polls(polls)
 
 
 def bt_check_timeouts() -> None:

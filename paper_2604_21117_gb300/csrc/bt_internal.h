@@ -34,8 +34,10 @@ struct DevTree {
     int pin_levels;      // top levels copied to shared memory by the descent
     uint32_t pin_bytes;  // bytes from the root's block to the end of those levels
     int warps;           // warps per descent block
-    int staging;         // 0: 16-byte cp.async per lane, 1: one bulk copy (TMA) per node block
+    int staging;         // BT_STAGE_*: pipelined (default), or synchronous with cp.async / bulk copies
     int lane_queries;    // queries per lane of the plain descent: 1 (32 per warp) or 2 (64 per warp)
+    int inner_stage;     // pipelined descent: inner levels read through L1 (0) or staged with cp.async (1)
+    int rank_ballot;     // pipelined descent: leaf rank by binary search (0) or warp ballot + popc (1)
     // Splitters of the batch partition: the largest keys of nsplit evenly
     // spaced leaves, and nsplit + 1 reciprocal widths of the key segments
     // they bound (part_sort.cuh).
@@ -69,12 +71,28 @@ struct PaperTree {
 // Whole top levels (never the leaves) whose bytes fit `budget`, root first.
 void set_pin_levels(DevTree &d, const bt_info &info, uint32_t budget);
 
+// Host-side launch facts, cached per device and safe to call from any
+// thread: the current device's SM count, resident blocks per SM of a kernel
+// at a block shape, and the kernel's dynamic shared-memory limit raised to
+// `bytes` (once per device and kernel).
+cudaError_t dev_sm_count(int *sms);
+cudaError_t blocks_per_sm(const void *kern, int threads, int dyn_smem, int *out);
+cudaError_t ensure_dyn_smem(const void *kern, int bytes);
+
+// Poll limit of the first bounded wait in the descent (bt_debug_set_wait_polls).
+uint32_t first_wait_polls();
+
 }  // namespace btgb
 
 struct bt_tree {
     btgb::DevTree dev;
     bt_info info;
     void *d_image;
+    // L2 access-policy window of the descent (bt_tree_set_l2_window): the
+    // non-pinned inner levels, marked persisting; 0 bytes = none.
+    const void *l2_base;
+    uint64_t l2_bytes;
+    float l2_hit_ratio;
     btgb::PaperTree paper;  // valid once d_paper is set (bt_paper_layout_build)
     void *d_paper;
 };

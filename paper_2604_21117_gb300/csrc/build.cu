@@ -6,10 +6,14 @@
 // are written directly in structure-of-arrays form from the sorted keys.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include "bt_internal.h"
@@ -78,6 +82,66 @@ static inline int key_cmp(const void *h_keys, uint64_t a, uint64_t b, int kb)
     return (x > y) - (x < y);
 }
 
+namespace {
+std::mutex g_launch_mu;
+std::map<int, int> g_sms;                                           // device -> SMs
+std::map<std::tuple<int, const void *, int, int>, int> g_occ;       // (device, kernel, threads, smem)
+std::map<std::pair<int, const void *>, int> g_dyn;                  // (device, kernel) -> limit set
+std::atomic<uint32_t> g_first_wait_polls{BT_DEFAULT_WAIT_POLLS};
+}  // namespace
+
+uint32_t first_wait_polls() { return g_first_wait_polls.load(std::memory_order_relaxed); }
+
+cudaError_t dev_sm_count(int *sms)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_launch_mu);
+    auto it = g_sms.find(dev);
+    if (it == g_sms.end()) {
+        int v = 0;
+        e = cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        it = g_sms.emplace(dev, v).first;
+    }
+    *sms = it->second;
+    return cudaSuccess;
+}
+
+cudaError_t blocks_per_sm(const void *kern, int threads, int dyn_smem, int *out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_launch_mu);
+    const auto key = std::make_tuple(dev, kern, threads, dyn_smem);
+    auto it = g_occ.find(key);
+    if (it == g_occ.end()) {
+        int b = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, threads, static_cast<size_t>(dyn_smem));
+        if (e != cudaSuccess) return e;
+        it = g_occ.emplace(key, b > 0 ? b : 1).first;
+    }
+    *out = it->second;
+    return cudaSuccess;
+}
+
+cudaError_t ensure_dyn_smem(const void *kern, int bytes)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_launch_mu);
+    const auto key = std::make_pair(dev, kern);
+    auto it = g_dyn.find(key);
+    if (it != g_dyn.end() && it->second >= bytes) return cudaSuccess;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    g_dyn[key] = bytes;
+    return cudaSuccess;
+}
+
 void set_pin_levels(DevTree &d, const bt_info &info, uint32_t budget)
 {
     d.pin_levels = 0;
@@ -111,10 +175,60 @@ extern "C" bt_status bt_tree_set_lane_queries(bt_tree *t, uint32_t per_lane)
 
 extern "C" bt_status bt_tree_set_staging(bt_tree *t, uint32_t mode)
 {
-    if (!t || mode > 1) return BT_ERR_ARG;
+    if (!t || mode > BT_STAGE_PIPELINED) return BT_ERR_ARG;
     t->dev.staging = static_cast<int>(mode);
     return BT_OK;
 }
+
+extern "C" bt_status bt_tree_set_descent(bt_tree *t, uint32_t inner_staged, uint32_t rank_ballot)
+{
+    if (!t || inner_staged > 1 || rank_ballot > 1) return BT_ERR_ARG;
+    t->dev.inner_stage = static_cast<int>(inner_staged);
+    t->dev.rank_ballot = static_cast<int>(rank_ballot);
+    return BT_OK;
+}
+
+extern "C" bt_status bt_tree_set_l2_window(bt_tree *t, uint64_t max_bytes)
+{
+    if (!t) return BT_ERR_ARG;
+    t->l2_base = nullptr;
+    t->l2_bytes = 0;
+    t->l2_hit_ratio = 0.0f;
+    const DevTree &d = t->dev;
+    if (max_bytes == 0 || d.height < 2 || d.pin_levels >= d.height - 1) return BT_OK;
+    // the inner levels below the pinned ones: contiguous from level pin_levels
+    // to the start of the leaf level
+    const uint64_t lo = t->info.level_key_offset[d.pin_levels];
+    const uint64_t hi = t->info.level_key_offset[d.height - 1];
+    int dev = 0, max_win = 0, max_persist = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&max_win, cudaDevAttrMaxAccessPolicyWindowSize, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, dev);
+    if (e != cudaSuccess) {
+        set_error_detail("L2 window attributes", e);
+        return BT_ERR_CUDA;
+    }
+    uint64_t bytes = hi - lo;
+    if (bytes > max_bytes) bytes = max_bytes;
+    if (bytes > static_cast<uint64_t>(max_win)) bytes = static_cast<uint64_t>(max_win);
+    if (bytes == 0 || max_persist <= 0) return BT_OK;
+    // the context's persisting set-aside (this process only; it ends with it)
+    size_t cur = 0;
+    e = cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize);
+    const size_t want = bytes < static_cast<uint64_t>(max_persist) ? bytes : static_cast<size_t>(max_persist);
+    if (e == cudaSuccess && cur < want) e = cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want);
+    if (e == cudaSuccess) e = cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize);
+    if (e != cudaSuccess) {
+        set_error_detail("persisting L2 limit", e);
+        return BT_ERR_CUDA;
+    }
+    t->l2_base = static_cast<const unsigned char *>(t->d_image) + lo;
+    t->l2_bytes = bytes;
+    t->l2_hit_ratio = cur >= bytes ? 1.0f : static_cast<float>(cur) / static_cast<float>(bytes);
+    return BT_OK;
+}
+
+extern "C" void bt_debug_set_wait_polls(uint32_t polls) { g_first_wait_polls.store(polls); }
 
 extern "C" const char *bt_last_error_detail(void) { return g_detail; }
 
@@ -223,6 +337,7 @@ extern "C" bt_status bt_build(const void *h_keys, const void *h_vals, uint64_t n
     // kept in shared memory (bt_tree_set_launch / bt_autotune change them).
     d.warps = 8;
     d.lane_queries = 1;
+    d.staging = BT_STAGE_PIPELINED;
     set_pin_levels(d, t->info, 16384);
 
     // Shape arithmetic: children (or keys, for leaves) per node.

@@ -26,6 +26,10 @@ struct bt_forest {
 
 namespace btgb {
 
+// Work-list entries rejected by k_forest (tree out of range, or queries
+// beyond the arrays); read and cleared by bt_forest_bad_batches.
+__device__ unsigned long long g_bt_bad_batches;
+
 __device__ __forceinline__ void fcp_async16(void *smem_dst, const void *gsrc)
 {
     const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
@@ -108,10 +112,10 @@ constexpr int kForestSlots = 8;
 constexpr int kForestMaxBlock = 512;  // bytes of the largest node block (m = 64, 8-byte keys)
 
 template <typename K, typename V>
-__global__ void __launch_bounds__(512) k_forest(const DevTree *__restrict__ trees, const bt_batch_desc *__restrict__ batches,
-                                                uint32_t nb, const uint32_t *__restrict__ chunk_start,
-                                                const K *__restrict__ q, V *__restrict__ out_v,
-                                                uint8_t *__restrict__ out_f)
+__global__ void __launch_bounds__(512) k_forest(const DevTree *__restrict__ trees, uint32_t ntrees,
+                                                const bt_batch_desc *__restrict__ batches, uint32_t nb,
+                                                const uint32_t *__restrict__ chunk_start, const K *__restrict__ q,
+                                                uint64_t nq, V *__restrict__ out_v, uint8_t *__restrict__ out_f)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -129,6 +133,12 @@ __global__ void __launch_bounds__(512) k_forest(const DevTree *__restrict__ tree
                 hi = mid - 1;
         }
         const bt_batch_desc bd = batches[lo];
+        // a descriptor naming a tree outside the forest, or queries beyond
+        // the arrays, is skipped (nothing written) and counted
+        if (bd.tree >= ntrees || bd.offset > nq || bd.count > nq - bd.offset) {
+            if (lane == 0 && c == chunk_start[lo]) atomicAdd(&g_bt_bad_batches, 1ull);
+            continue;
+        }
         const uint32_t j = (c - chunk_start[lo]) * 32u + lane;
         const bool valid = j < bd.count;
         const DevTree &t = trees[bd.tree];
@@ -187,23 +197,20 @@ __global__ void __launch_bounds__(512) k_forest(const DevTree *__restrict__ tree
 
 template <typename K, typename V>
 static cudaError_t forest_launch(const bt_forest *f, const bt_batch_desc *d_b, uint32_t nb, uint32_t *chunk_start,
-                                 const void *q, void *ov, uint8_t *of, uint32_t warps, cudaStream_t s)
+                                 const void *q, uint64_t nq, void *ov, uint8_t *of, uint32_t warps, cudaStream_t s)
 {
     const int threads = static_cast<int>(warps) * 32;
     const int smem = static_cast<int>(warps) * (kForestSlots * kForestMaxBlock + 32 * 4);
     auto kern = k_forest<K, V>;
-    static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                         16 * (kForestSlots * kForestMaxBlock + 32 * 4));
-    if (attr != cudaSuccess) return attr;
-    int per_sm = 0, dev = 0, sms = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
-    if (e == cudaSuccess) e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = ensure_dyn_smem(reinterpret_cast<const void *>(kern), 16 * (kForestSlots * kForestMaxBlock + 32 * 4));
+    int per_sm = 0, sms = 0;
+    if (e == cudaSuccess) e = blocks_per_sm(reinterpret_cast<const void *>(kern), threads, smem, &per_sm);
+    if (e == cudaSuccess) e = dev_sm_count(&sms);
     if (e != cudaSuccess) return e;
     k_forest_plan<<<1, 1024, 0, s>>>(d_b, nb, chunk_start);
     const unsigned grid = static_cast<unsigned>(sms * (per_sm > 0 ? per_sm : 1));
-    kern<<<grid, threads, smem, s>>>(f->d_trees, d_b, nb, chunk_start, static_cast<const K *>(q), static_cast<V *>(ov),
-                                     of);
+    kern<<<grid, threads, smem, s>>>(f->d_trees, f->count, d_b, nb, chunk_start, static_cast<const K *>(q), nq,
+                                     static_cast<V *>(ov), of);
     return cudaGetLastError();
 }
 
@@ -252,7 +259,7 @@ extern "C" void bt_forest_free(bt_forest *f)
 extern "C" uint64_t bt_forest_workspace_bytes(uint32_t nbatches) { return (static_cast<uint64_t>(nbatches) + 1) * 4; }
 
 extern "C" bt_status bt_forest_search(const bt_forest *f, const bt_batch_desc *d_batches, uint32_t nbatches,
-                                      const void *d_queries, void *d_out_vals, uint8_t *d_out_found,
+                                      const void *d_queries, uint64_t nq, void *d_out_vals, uint8_t *d_out_found,
                                       void *d_workspace, uint64_t ws_bytes, uint32_t warps_per_block,
                                       bt_stream stream)
 {
@@ -267,22 +274,39 @@ extern "C" bt_status bt_forest_search(const bt_forest *f, const bt_batch_desc *d
     cudaError_t e;
     if (f->key_bytes == 8) {
         if (f->val_bytes == 8)
-            e = forest_launch<uint64_t, uint64_t>(f, d_batches, nbatches, cs, d_queries, d_out_vals, d_out_found,
-                                                  warps_per_block, s);
+            e = forest_launch<uint64_t, uint64_t>(f, d_batches, nbatches, cs, d_queries, nq, d_out_vals,
+                                                  d_out_found, warps_per_block, s);
         else
-            e = forest_launch<uint64_t, uint32_t>(f, d_batches, nbatches, cs, d_queries, d_out_vals, d_out_found,
-                                                  warps_per_block, s);
+            e = forest_launch<uint64_t, uint32_t>(f, d_batches, nbatches, cs, d_queries, nq, d_out_vals,
+                                                  d_out_found, warps_per_block, s);
     } else {
         if (f->val_bytes == 8)
-            e = forest_launch<uint32_t, uint64_t>(f, d_batches, nbatches, cs, d_queries, d_out_vals, d_out_found,
-                                                  warps_per_block, s);
+            e = forest_launch<uint32_t, uint64_t>(f, d_batches, nbatches, cs, d_queries, nq, d_out_vals,
+                                                  d_out_found, warps_per_block, s);
         else
-            e = forest_launch<uint32_t, uint32_t>(f, d_batches, nbatches, cs, d_queries, d_out_vals, d_out_found,
-                                                  warps_per_block, s);
+            e = forest_launch<uint32_t, uint32_t>(f, d_batches, nbatches, cs, d_queries, nq, d_out_vals,
+                                                  d_out_found, warps_per_block, s);
     }
     if (e != cudaSuccess) {
         set_error_detail("forest search launch", e);
         return BT_ERR_CUDA;
     }
+    return BT_OK;
+}
+
+extern "C" bt_status bt_forest_bad_batches(uint64_t *out)
+{
+    if (!out) return BT_ERR_ARG;
+    unsigned long long v = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(&v, g_bt_bad_batches, sizeof(v));
+    if (e == cudaSuccess && v) {
+        const unsigned long long zero = 0;
+        e = cudaMemcpyToSymbol(g_bt_bad_batches, &zero, sizeof(zero));
+    }
+    if (e != cudaSuccess) {
+        set_error_detail("rejected-batch counter", e);
+        return BT_ERR_CUDA;
+    }
+    *out = v;
     return BT_OK;
 }

@@ -74,4 +74,31 @@ struct KeyOps<Key32> {
 template <typename K>
 using RawOf = typename KeyOps<K>::Raw;
 
+// One query of the partitioned batch: the key as the caller gave it, its
+// input position, and its local-sort digit (16 bytes for integer keys, 48
+// for 32-byte keys), so that each query moves with one vector store.
+template <typename K>
+struct alignas(16) PartRec {
+    RawOf<K> key;
+    uint32_t idx;
+    uint32_t digit;
+};
+
+// Load query `pos` of a batch: from the partition's records when given,
+// else from the key array and the optional position array (identity when
+// absent).
+template <typename K>
+__device__ __forceinline__ void load_query(const RawOf<K> *q, const uint32_t *qidx, const PartRec<K> *recs,
+                                           uint64_t pos, K &key, uint32_t &dst)
+{
+    if (recs) {
+        const PartRec<K> r = recs[pos];
+        key = KeyOps<K>::from_raw(r.key);
+        dst = r.idx;
+    } else {
+        key = KeyOps<K>::load(q, pos);
+        dst = qidx ? qidx[pos] : static_cast<uint32_t>(pos);
+    }
+}
+
 }  // namespace btgb

@@ -11,8 +11,9 @@
 namespace {
 
 // Scratch for one search of up to BT_NOALLOC_MAX_QUERIES integer queries
-// (the partitioned batch and the partition's bucket totals): 2 MiB.
-constexpr uint64_t kNoallocScratchBytes = 2ull << 20;
+// (the partitioned batch, scattered and sorted, and the partition's bucket
+// counters): 4 MiB.
+constexpr uint64_t kNoallocScratchBytes = 4ull << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
 constexpr int kMaxDevices = 64;

@@ -2,13 +2,12 @@
 //
 // The paper sorts the query batch so that all queries routed to one node
 // are adjacent and served by one node fetch (Sec. IV-A, Sec. IV-E).  What
-// the warp-level descent needs is weaker: each run of 32 consecutive
-// queries should cover a narrow key range.  A counting sort on a bucket
-// number that is monotone in the key gives that in two passes over the
-// batch:
+// the warp-level descent needs is that each run of 32 consecutive queries
+// covers as narrow a key range as a sorted batch would.  A two-level
+// counting sort on a bucket number that is monotone in the key gives that:
 //
-//   bucket(q) = (c << r) | s      (or c >> cshift when fewer bits are asked
-//                                   for than c has)
+//   f(q) = (c << r) | s      (or c >> cshift when fewer bits are asked for
+//                               than c has), on `bits` bits in all
 //     c  = how many of the tree's splitters are smaller than q.  The
 //          splitters are the largest keys of evenly spaced leaves (at most
 //          kSplitSlots of them, built with the tree), so c is q's rank among
@@ -17,20 +16,24 @@
 //          between the segment's bounds (fp32; monotone in q).  32-byte keys
 //          interpolate on the 8 bytes that follow the bytes the segment's
 //          bounds (hence all its keys) share.
+//   coarse(q) = f(q) >> lb,   digit(q) = f(q) & (2^lb - 1).
 //
-//   k_part_hist     per block, the bucket counts of a slice of the batch in
-//                   shared memory, added to the global totals once per
-//                   non-zero bucket (a hot key costs one global atomic per
-//                   block); the last block to finish (a ticket counter, no
-//                   waiting) turns the totals into exclusive bucket starts.
-//   k_part_scatter  per block and round of queries: shared-memory bucket
-//                   counts, one global atomic per non-zero bucket to
-//                   reserve its run, then each query's slot in the run from
-//                   a shared-memory atomic; the query and its input position
-//                   are written there.
+// One cooperative launch, k_partition (every block resident; two bounded
+// grid barriers), with the batch cut into one slice per block:
+//   count     the slice's coarse buckets in shared memory, added to global
+//             totals with one atomic per bucket whose return value is the
+//             block's offset inside that bucket;
+//   scatter   bucket starts by a scan of the totals; every query takes its
+//             bucket's next position (a shared-memory atomic) and is written
+//             there as one record (key, input position, digit);
+//   sort      groups of threads order the coarse buckets by digit, in
+//             place, several buckets per block at once.  Buckets of more
+//             than part_tile<K>() queries (a hot key, or a coarse bucket far
+//             above its average size) keep the scatter's order.
 //
-// Result: the batch ordered by bucket; the order of queries within one
-// bucket is unspecified (it depends on the order of the atomics).
+// Result: the batch ordered by coarse bucket, and inside every coarse bucket
+// of at most part_tile<K>() queries by f; queries with equal f (and in the
+// larger buckets, equal coarse buckets) come in an unspecified order.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -43,9 +46,23 @@ namespace btgb {
 
 constexpr int kSplitSlots = 1023;   // splitters per tree, at most
 constexpr int kRadixBits = 12;      // pre-index of the splitters by leading key bits
-constexpr int kSplitBits = 10;      // bits of c with the full table
-constexpr int kMaxPartBits = 13;    // bucket bits, at most (2^13 counters in shared memory)
-constexpr int kPartThreads = 1024;
+constexpr int kMaxCoarseBits = 12;  // coarse buckets: at most 2^12 counters in shared memory
+constexpr int kLocalBits = 9;       // digit bits of the local sort: 2^9 counters
+constexpr int kMaxPartBits = kMaxCoarseBits + kLocalBits;
+constexpr int kPartThreads = 512;
+// The local sort: groups of kSortThreads threads, each ordering one coarse
+// bucket at a time.
+constexpr int kSortThreads = 128;
+constexpr int kSortGroups = kPartThreads / kSortThreads;
+
+// Largest coarse bucket the local sort orders (one group of threads, the
+// bucket's records in registers; larger buckets, a hot key, keep the
+// scatter's order).
+template <typename K>
+__host__ __device__ constexpr int part_tile()
+{
+    return sizeof(K) > 8 ? 256 : 1024;
+}
 
 // Per-search view of the tree's splitter table.
 template <typename K>
@@ -61,34 +78,73 @@ struct PartNorm {
     K kmax;                 // largest key: upper bound of the last segment
     uint32_t nsplit;
     int r;                  // interpolation bits within a segment
-    int cshift;             // with r == 0: bucket = c >> cshift (fewer bits than c has)
+    int cshift;             // with r == 0: f = c >> cshift (fewer bits than c has)
+    int lb;                 // digit bits: coarse = f >> lb
     float scale;            // 2^r
 };
 
 // Shared-memory copy of the splitters, padded with all-ones keys so that a
-// branchless binary search of kSplitBits probes finds c.
+// branchless binary search of ten probes finds c.
 template <typename K>
-struct PartSmem {
+struct __align__(16) PartSmem {
     K sp[kSplitSlots + 1];
     float inv[kSplitSlots + 1];
     unsigned char off[kSplitSlots + 1];
-    uint16_t R[(1 << kRadixBits) + 1];
+    uint16_t R[(1 << kRadixBits) + 8];  // whole 16-byte pieces
     uint32_t scan_tmp[32];
     uint32_t last;
 };
 
+__device__ __forceinline__ void part_cp_async16(void *smem_dst, const void *gsrc)
+{
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+
+// Copy the splitter tables to shared memory in one round of 16-byte
+// asynchronous copies (every table starts on a 256-byte boundary of the
+// tree image, and the image pads each to the next such boundary, so whole
+// 16-byte pieces stay inside it), then pad the splitters beyond nsplit with
+// all-ones keys.  Ends with a block barrier.
 template <typename K>
 __device__ __forceinline__ void part_load_tables(PartSmem<K> &S, const PartNorm<K> &pn)
 {
-    for (int i = threadIdx.x; i <= kSplitSlots; i += blockDim.x) {
-        S.sp[i] = i < static_cast<int>(pn.nsplit) ? pn.split[i] : KeyOps<K>::ones();
-        S.inv[i] = i <= static_cast<int>(pn.nsplit) ? pn.split_inv[i] : 0.0f;
-        S.off[i] = (pn.split_off && i <= static_cast<int>(pn.nsplit)) ? pn.split_off[i] : 0;
+    const uint32_t ns = pn.nsplit;
+    const uint32_t sp_pieces = (ns * static_cast<uint32_t>(sizeof(K)) + 15u) / 16u;
+    const uint32_t inv_pieces = ((ns + 1u) * 4u + 15u) / 16u;
+    const uint32_t off_pieces = pn.split_off ? ((ns + 1u) + 15u) / 16u : 0u;
+    const uint32_t r_pieces = pn.split_R ? (((1u << kRadixBits) + 1u) * 2u + 15u) / 16u : 0u;
+    const uint32_t total = sp_pieces + inv_pieces + off_pieces + r_pieces;
+    for (uint32_t i = threadIdx.x; i < total; i += blockDim.x) {
+        uint32_t j = i;
+        if (j < sp_pieces) {
+            part_cp_async16(reinterpret_cast<unsigned char *>(S.sp) + 16 * j,
+                            reinterpret_cast<const unsigned char *>(pn.split) + 16 * j);
+            continue;
+        }
+        j -= sp_pieces;
+        if (j < inv_pieces) {
+            part_cp_async16(reinterpret_cast<unsigned char *>(S.inv) + 16 * j,
+                            reinterpret_cast<const unsigned char *>(pn.split_inv) + 16 * j);
+            continue;
+        }
+        j -= inv_pieces;
+        if (j < off_pieces) {
+            part_cp_async16(S.off + 16 * j, pn.split_off + 16 * j);
+            continue;
+        }
+        j -= off_pieces;
+        part_cp_async16(reinterpret_cast<unsigned char *>(S.R) + 16 * j,
+                        reinterpret_cast<const unsigned char *>(pn.split_R) + 16 * j);
     }
-    if (pn.split_R)
-        for (int i = threadIdx.x; i <= (1 << kRadixBits); i += blockDim.x) S.R[i] = pn.split_R[i];
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+    __syncthreads();
+    for (uint32_t i = ns + threadIdx.x; i <= static_cast<uint32_t>(kSplitSlots); i += blockDim.x)
+        S.sp[i] = KeyOps<K>::ones();
+    __syncthreads();
 }
 
+// f(q) for integer keys.
 template <typename K>
 __device__ __forceinline__ uint32_t part_bucket(const PartSmem<K> &S, const PartNorm<K> &pn, K q)
 {
@@ -130,6 +186,7 @@ __device__ __forceinline__ uint64_t key32_window(const Key32 &k, int p)
     return s ? (hi << s) | (lo >> (64 - s)) : hi;
 }
 
+// f(q) for 32-byte keys.
 __device__ __forceinline__ uint32_t part_bucket(const PartSmem<Key32> &S, const PartNorm<Key32> &pn, const Key32 &q)
 {
     uint32_t c = 0;
@@ -167,13 +224,6 @@ __device__ __forceinline__ uint32_t part_bucket(const PartSmem<Key32> &S, const 
     return (c << pn.r) | static_cast<uint32_t>(x);
 }
 
-__device__ __forceinline__ unsigned part_lanemask_lt()
-{
-    unsigned r;
-    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(r));
-    return r;
-}
-
 // Block-wide exclusive scan of one value per thread; `tmp` holds 32 words.
 __device__ __forceinline__ uint32_t part_block_excl_scan(uint32_t v, uint32_t *tmp)
 {
@@ -199,142 +249,330 @@ __device__ __forceinline__ uint32_t part_block_excl_scan(uint32_t v, uint32_t *t
     return r;
 }
 
-// Queries a block of k_part_scatter holds (in registers) per round.
-template <typename K>
-constexpr int part_per_thread()
+// In-place exclusive scan of n counters in shared memory (n a multiple of
+// 4, at most 8 * blockDim.x); every thread of the block must call it.
+__device__ __forceinline__ void part_scan_smem(uint32_t *cnt, uint32_t n, uint32_t *tmp)
 {
-    return sizeof(K) > 8 ? 4 : 8;
+    const uint32_t per = (n + blockDim.x - 1) / blockDim.x;  // at most 8
+    const uint32_t j0 = threadIdx.x * per;
+    uint32_t v[8];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const uint32_t j = j0 + k;
+        v[k] = (static_cast<uint32_t>(k) < per && j < n) ? cnt[j] : 0u;
+        sum += v[k];
+    }
+    uint32_t run = part_block_excl_scan(sum, tmp);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const uint32_t j = j0 + k;
+        if (static_cast<uint32_t>(k) < per && j < n) {
+            cnt[j] = run;
+            run += v[k];
+        }
+    }
+    __syncthreads();
 }
 
-// Bucket histogram.  Each block counts the buckets of one contiguous slice
-// of the batch in shared memory (dynamic, nb words), then adds its non-zero
-// counts to total[] (nb words, zero on entry).  total[nb] is a ticket (zero
-// on entry): the last block to finish turns total[] into exclusive bucket
-// starts.  nb is a multiple of 4.
+// Blocks of the partition, at most.
+constexpr uint32_t kMaxPartBlocks = 1024;
+
+// Bounded waits of the partition's grid barrier that gave up (the results of
+// that search are invalid); read and cleared by bt_check_timeouts.
+static __device__ unsigned int g_part_timeouts;
+
+// Queries of its slice a partition block keeps in shared memory between
+// counting and scattering (integer keys; 32-byte keys are read again).
 template <typename K>
-__global__ void __launch_bounds__(kPartThreads) k_part_hist(const RawOf<K> *__restrict__ q, uint64_t nq, PartNorm<K> pn,
-                                                            uint32_t *__restrict__ total, uint32_t nb)
+__host__ __device__ constexpr uint32_t part_cache()
+{
+    return sizeof(K) > 8 ? 0u : 4096u;
+}
+
+// Dynamic shared memory of k_partition for nb coarse buckets: the block's
+// counts / next positions (nb words), the bucket starts (nb + 4 words), then
+// an area holding first the cached slice (keys, then f) and later every
+// sort group's digit counters.
+template <typename K>
+__host__ __device__ constexpr int part_area()
+{
+    return part_cache<K>() * static_cast<int>(sizeof(RawOf<K>) + 4) > kSortGroups * ((1 << kLocalBits) + 8) * 4
+               ? part_cache<K>() * static_cast<int>(sizeof(RawOf<K>) + 4)
+               : kSortGroups * ((1 << kLocalBits) + 8) * 4;
+}
+
+template <typename K>
+__host__ __device__ constexpr int part_dyn(uint32_t nb)
+{
+    return static_cast<int>((nb + (nb + 4)) * 4u) + part_area<K>();
+}
+
+// A record read through L2 (written by another block of the same launch).
+template <typename K>
+__device__ __forceinline__ PartRec<K> ld_rec_cg(const PartRec<K> *p)
+{
+    static_assert(sizeof(PartRec<K>) % 16 == 0, "records are whole 16-byte pieces");
+    PartRec<K> r;
+    const uint4 *src = reinterpret_cast<const uint4 *>(p);
+    uint4 *dst = reinterpret_cast<uint4 *>(&r);
+#pragma unroll
+    for (int i = 0; i < static_cast<int>(sizeof(PartRec<K>) / 16); ++i) dst[i] = __ldcg(src + i);
+    return r;
+}
+
+// Grid-wide barrier of a cooperative launch (every block resident): thread 0
+// counts its block's arrival on *ctr (zero before the launch) and waits, at
+// most `polls` polls, until all gridDim.x blocks have arrived.  False if the
+// wait gave up.
+__device__ __forceinline__ bool part_grid_sync(unsigned int *ctr, uint32_t polls, uint32_t *flag)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(ctr, 1u);
+        uint32_t ok = 0;
+        for (uint32_t i = 0; i < polls; ++i) {
+            unsigned int v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+            if (v >= gridDim.x) {
+                ok = 1;
+                break;
+            }
+            __nanosleep(32);
+        }
+        *flag = ok;
+    }
+    __syncthreads();
+    return *flag != 0;
+}
+
+// Named barrier of sort group g (ids 1.. ; 0 is __syncthreads).
+__device__ __forceinline__ void part_group_sync(uint32_t g)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(kSortThreads) : "memory");
+}
+
+// In-place exclusive scan of n counters (a multiple of 4, at most
+// 8 * kSortThreads) by one sort group; tmp holds a word per warp of the group.
+__device__ __forceinline__ void part_group_scan(uint32_t *cnt, uint32_t n, uint32_t *tmp, uint32_t g, uint32_t gtid)
+{
+    const uint32_t lane = gtid & 31, w = gtid >> 5;
+    const uint32_t per = (n + kSortThreads - 1) / kSortThreads;
+    const uint32_t j0 = gtid * per;
+    uint32_t v[8];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const uint32_t j = j0 + k;
+        v[k] = (static_cast<uint32_t>(k) < per && j < n) ? cnt[j] : 0u;
+        sum += v[k];
+    }
+    uint32_t x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= static_cast<uint32_t>(o)) x += y;
+    }
+    if (lane == 31) tmp[w] = x;
+    part_group_sync(g);
+    uint32_t run = x - sum;
+    for (uint32_t k = 0; k < w; ++k) run += tmp[k];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const uint32_t j = j0 + k;
+        if (static_cast<uint32_t>(k) < per && j < n) {
+            cnt[j] = run;
+            run += v[k];
+        }
+    }
+    part_group_sync(g);
+}
+
+// The whole partition in one cooperative launch; block g owns slice g of
+// the batch (ceil(nq / gridDim.x) queries).
+//   1. Count the slice's coarse buckets in shared memory (keeping each key
+//      and its f in shared memory when the slice fits part_cache).
+//   2. Add every count to total[j] (nb words, zero on entry) with one atomic
+//      whose return value -- the bucket's queries counted by blocks whose
+//      atomic came first -- is the block's offset inside bucket j.
+//   -- grid barrier on total[nb] --
+//   3. Bucket starts: the exclusive scan of the totals (every block); the
+//      block's next position in bucket j is start[j] + offset[j].
+//   4. Every query of the slice takes its bucket's next position (a
+//      shared-memory atomic) and is written there as one record.
+//   -- grid barrier on total[nb + 1] --
+//   5. Local sort, in place: groups of kSortThreads threads order the
+//      coarse buckets of at most part_tile records by digit, one bucket per
+//      group at a time (records in registers, ranks among equal digits from
+//      shared-memory atomics, a scan of the digit counts).
+// A barrier that gives up is counted (g_part_timeouts) and its block
+// stops; that search's results are then invalid.
+template <typename K>
+__global__ void __launch_bounds__(kPartThreads, 2) k_partition(const RawOf<K> *__restrict__ q, uint64_t nq,
+                                                               PartNorm<K> pn, unsigned int *__restrict__ total,
+                                                               uint32_t nb, PartRec<K> *__restrict__ rec,
+                                                               uint32_t polls)
 {
     __shared__ PartSmem<K> S;
-    extern __shared__ uint32_t cnt[];
+    extern __shared__ __align__(16) unsigned char dsm[];
+    constexpr int U = 4;
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(dsm);
+    uint32_t *st = cnt + nb;
+    unsigned char *area = reinterpret_cast<unsigned char *>(st + nb + 4);  // nb is a multiple of 4
+    RawOf<K> *ck = reinterpret_cast<RawOf<K> *>(area);
+    uint32_t *cf = reinterpret_cast<uint32_t *>(ck + part_cache<K>());
     part_load_tables(S, pn);
     for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x) cnt[j] = 0;
     __syncthreads();
     const uint64_t per = (nq + gridDim.x - 1) / gridDim.x;
-    const uint64_t s0 = blockIdx.x * per, s1 = s0 + per < nq ? s0 + per : nq;
-    constexpr int U = 4;
-    for (uint64_t i0 = s0 + threadIdx.x; i0 < s1; i0 += static_cast<uint64_t>(U) * blockDim.x) {
+    const uint64_t s0 = blockIdx.x * per < nq ? blockIdx.x * per : nq;
+    const uint64_t s1 = s0 + per < nq ? s0 + per : nq;
+    const uint32_t ns = static_cast<uint32_t>(s1 - s0);
+    const bool cached = ns <= part_cache<K>();
+
+    // 1. counts
+    for (uint32_t i0 = threadIdx.x; i0 < ns; i0 += U * blockDim.x) {
         RawOf<K> key[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const uint64_t i = i0 + static_cast<uint64_t>(u) * blockDim.x;
-            if (i < s1) key[u] = q[i];
+            const uint32_t i = i0 + u * blockDim.x;
+            if (i < ns) key[u] = q[s0 + i];
         }
 #pragma unroll
-        for (int u = 0; u < U; ++u)
-            if (i0 + static_cast<uint64_t>(u) * blockDim.x < s1)
-                atomicAdd(cnt + part_bucket(S, pn, KeyOps<K>::from_raw(key[u])), 1u);
-    }
-    __syncthreads();
-    for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x)
-        if (cnt[j]) atomicAdd(total + j, cnt[j]);
-    // The last block to get here scans the totals (every other block's adds
-    // are visible to it after their fences and its ticket).
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) S.last = (atomicAdd(total + nb, 1u) == gridDim.x - 1) ? 1u : 0u;
-    __syncthreads();
-    if (!S.last) return;
-    __threadfence();
-    const uint32_t groups = nb / 4;
-    const uint32_t per4 = (groups + blockDim.x - 1) / blockDim.x;  // uint4 groups per thread
-    uint4 *t4 = reinterpret_cast<uint4 *>(total);
-    const uint32_t g0 = threadIdx.x * per4;
-    uint4 v[4];  // nb <= 2^13 and 1024 threads: at most 2 groups per thread
-    uint32_t sum = 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const uint32_t g = g0 + k;
-        v[k] = (k < static_cast<int>(per4) && g < groups) ? __ldcg(t4 + g) : make_uint4(0, 0, 0, 0);
-        sum += v[k].x + v[k].y + v[k].z + v[k].w;
-    }
-    uint32_t run = part_block_excl_scan(sum, S.scan_tmp);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const uint32_t g = g0 + k;
-        if (k < static_cast<int>(per4) && g < groups) {
-            const uint32_t a0 = run, a1 = a0 + v[k].x, a2 = a1 + v[k].y, a3 = a2 + v[k].z;
-            run = a3 + v[k].w;
-            t4[g] = make_uint4(a0, a1, a2, a3);
+        for (int u = 0; u < U; ++u) {
+            const uint32_t i = i0 + u * blockDim.x;
+            if (i < ns) {
+                const uint32_t f = part_bucket(S, pn, KeyOps<K>::from_raw(key[u]));
+                if (cached) {
+                    ck[i] = key[u];
+                    cf[i] = f;
+                }
+                atomicAdd(cnt + (f >> pn.lb), 1u);
+            }
         }
+    }
+    __syncthreads();
+    // 2. offsets: all of a thread's atomics are issued before any result is used
+    {
+        constexpr int RPT = (1 << kMaxCoarseBits) / kPartThreads;
+        uint32_t cv[RPT];
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            const uint32_t j = threadIdx.x + k * blockDim.x;
+            cv[k] = j < nb ? cnt[j] : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < RPT; ++k)
+            if (cv[k]) cv[k] = atomicAdd(total + threadIdx.x + k * blockDim.x, cv[k]);
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            const uint32_t j = threadIdx.x + k * blockDim.x;
+            if (j < nb) cnt[j] = cv[k];
+        }
+    }
+    if (!part_grid_sync(total + nb, polls, &S.last)) {
+        if (threadIdx.x == 0) atomicAdd(&g_part_timeouts, 1u);
+        return;
+    }
+    // 3. bucket starts and the block's next positions
+    for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x) st[j] = __ldcg(total + j);
+    __syncthreads();
+    part_scan_smem(st, nb, S.scan_tmp);
+    for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x) cnt[j] += st[j];
+    if (threadIdx.x == 0) st[nb] = static_cast<uint32_t>(nq);
+    __syncthreads();
+    // 4. records
+    const uint32_t dmask = (1u << pn.lb) - 1u;
+    for (uint32_t i0 = threadIdx.x; i0 < ns; i0 += U * blockDim.x) {
+        RawOf<K> key[U];
+        uint32_t f[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t i = i0 + u * blockDim.x;
+            if (i < ns) {
+                if (cached) {
+                    key[u] = ck[i];
+                    f[u] = cf[i];
+                } else {
+                    key[u] = q[s0 + i];
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t i = i0 + u * blockDim.x;
+            if (i < ns) {
+                if (!cached) f[u] = part_bucket(S, pn, KeyOps<K>::from_raw(key[u]));
+                const uint32_t pos = atomicAdd(cnt + (f[u] >> pn.lb), 1u);
+                if (pos < nq) {  // always true when the counts agree; keeps a stray write in bounds
+                    PartRec<K> r;
+                    r.key = key[u];
+                    r.idx = static_cast<uint32_t>(s0 + i);
+                    r.digit = f[u] & dmask;
+                    rec[pos] = r;
+                }
+            }
+        }
+    }
+    if (pn.lb == 0) return;
+    if (!part_grid_sync(total + nb + 1, polls, &S.last)) {
+        if (threadIdx.x == 0) atomicAdd(&g_part_timeouts, 1u);
+        return;
+    }
+    // 5. local sorts, in place: the block's threads form kSortGroups groups
+    // of kSortThreads, each ordering one coarse bucket of at most part_tile
+    // records at a time by digit (records in registers, ranks among equal
+    // digits from shared-memory atomics, a scan of the digit counts; the
+    // group synchronises on its own named barrier).
+    const uint32_t nd = 1u << pn.lb;
+    const uint32_t nscan = nd < 4 ? 4 : nd;  // the scan works on groups of 4 counters
+    const uint32_t grp = threadIdx.x / kSortThreads, gtid = threadIdx.x % kSortThreads;
+    uint32_t *gb = reinterpret_cast<uint32_t *>(area) + grp * ((1 << kLocalBits) + 8);
+    uint32_t *gtmp = gb + (1 << kLocalBits);  // per-warp partial sums of the group's scan
+    constexpr int EL = part_tile<K>() / kSortThreads;
+    for (uint32_t b = blockIdx.x * kSortGroups + grp; b < nb; b += gridDim.x * kSortGroups) {
+        const uint32_t bs = st[b];
+        const uint32_t n = st[b + 1] - bs;
+        if (n <= 1 || n > static_cast<uint32_t>(part_tile<K>())) continue;  // the same for the whole group
+        for (uint32_t j = gtid; j < nscan; j += kSortThreads) gb[j] = 0;
+        part_group_sync(grp);
+        PartRec<K> r[EL];
+        uint32_t rk[EL];
+#pragma unroll
+        for (int e = 0; e < EL; ++e) {
+            const uint32_t i = gtid + e * kSortThreads;
+            if (i < n) r[e] = ld_rec_cg(rec + bs + i);
+        }
+#pragma unroll
+        for (int e = 0; e < EL; ++e) {
+            const uint32_t i = gtid + e * kSortThreads;
+            if (i < n) rk[e] = atomicAdd(gb + (r[e].digit & (nd - 1u)), 1u);
+        }
+        part_group_sync(grp);
+        part_group_scan(gb, nscan, gtmp, grp, gtid);
+#pragma unroll
+        for (int e = 0; e < EL; ++e) {
+            const uint32_t i = gtid + e * kSortThreads;
+            if (i < n) {
+                const uint32_t p = gb[r[e].digit & (nd - 1u)] + rk[e];
+                if (p < n) rec[bs + p] = r[e];  // always true; keeps a stray write inside the bucket
+            }
+        }
+        part_group_sync(grp);
     }
 }
 
-// Scatter.  Each block takes up to part_per_thread * blockDim.x queries
-// per round: counts their buckets in shared memory, reserves each
-// non-zero bucket's run with one atomic on the global cursor (the bucket
-// starts from k_part_hist), then places every query at its run's next slot
-// (a shared-memory atomic) and writes it with its input position.
+// The records split into a key array and a position array (bt_sort_batch).
 template <typename K>
-__global__ void __launch_bounds__(kPartThreads) k_part_scatter(const RawOf<K> *__restrict__ q, uint64_t nq,
-                                                               PartNorm<K> pn, uint32_t *__restrict__ cursor,
-                                                               uint32_t nb, RawOf<K> *__restrict__ out_q,
-                                                               uint32_t *__restrict__ out_i)
+__global__ void k_part_unpack(const PartRec<K> *__restrict__ rec, uint64_t nq, RawOf<K> *__restrict__ out_q,
+                              uint32_t *__restrict__ out_i)
 {
-    __shared__ PartSmem<K> S;
-    extern __shared__ uint32_t cnt[];
-    constexpr int E = part_per_thread<K>();
-    part_load_tables(S, pn);
-    const uint64_t round = static_cast<uint64_t>(E) * blockDim.x;
-    for (uint64_t base = blockIdx.x * round; base < nq; base += gridDim.x * round) {
-        for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x) cnt[j] = 0;
-        __syncthreads();
-        RawOf<K> key[E];
-        uint32_t bk[E];
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const uint64_t i = base + static_cast<uint64_t>(e) * blockDim.x + threadIdx.x;
-            if (i < nq) key[e] = q[i];
-        }
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const uint64_t i = base + static_cast<uint64_t>(e) * blockDim.x + threadIdx.x;
-            if (i < nq) {
-                bk[e] = part_bucket(S, pn, KeyOps<K>::from_raw(key[e]));
-                atomicAdd(cnt + bk[e], 1u);
-            }
-        }
-        __syncthreads();
-        {
-            // reserve every non-zero bucket's run: all of a thread's atomics
-            // are issued before any result is used (one round trip)
-            constexpr int RPT = (1 << kMaxPartBits) / kPartThreads;
-            uint32_t cv[RPT];
-#pragma unroll
-            for (int k = 0; k < RPT; ++k) {
-                const uint32_t j = threadIdx.x + k * kPartThreads;
-                cv[k] = j < nb ? cnt[j] : 0u;
-            }
-#pragma unroll
-            for (int k = 0; k < RPT; ++k)
-                if (cv[k]) cv[k] = atomicAdd(cursor + threadIdx.x + k * kPartThreads, cv[k]);
-#pragma unroll
-            for (int k = 0; k < RPT; ++k) {
-                const uint32_t j = threadIdx.x + k * kPartThreads;
-                if (j < nb) cnt[j] = cv[k];
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const uint64_t i = base + static_cast<uint64_t>(e) * blockDim.x + threadIdx.x;
-            if (i < nq) {
-                const uint32_t pos = atomicAdd(cnt + bk[e], 1u);
-                out_q[pos] = key[e];
-                out_i[pos] = static_cast<uint32_t>(i);
-            }
-        }
-        __syncthreads();
+    for (uint64_t i = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; i < nq;
+         i += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+        const PartRec<K> r = rec[i];
+        out_q[i] = r.key;
+        out_i[i] = r.idx;
     }
 }
 

@@ -2,9 +2,9 @@
 //
 // For a key set and a sample batch, every fanout in {8, 16, 32, 64} is
 // built and the sample searched with every combination of warps per block
-// {4, 8, 16}, shared-memory pin budget {0, 16 KB, 48 KB}, node staging
-// mode (16-byte cp.async or bulk copy) and queries per lane {1, 2}; the
-// fastest
+// {4, 8, 16}, shared-memory pin budget {0, 16 KB, 48 KB} and descent design
+// (pipelined with inner levels through L1 or staged; synchronous with
+// cp.async or bulk-copy staging; two queries per lane); the fastest
 // combination (median of timed repetitions, CUDA events on the caller's
 // stream) wins and its tree is returned with those settings applied.
 #include <cuda_runtime.h>
@@ -78,7 +78,7 @@ extern "C" bt_status bt_autotune(const void *h_keys, const void *h_vals, uint64_
     const uint32_t warps[] = {4, 8, 16};
     const uint32_t pins[] = {0, 16384, 49152};
     bt_tree *keep = nullptr;
-    bt_tune b{0, 0, 0, 0, 1, 0.0f};
+    bt_tune b{0, 0, 0, 0, 1, 0, 0.0f};
     for (uint32_t m : fanouts) {
         bt_tree *t = nullptr;
         bt_status st = bt_build(h_keys, h_vals, n, key_w, val_w, m, stream, &t);
@@ -94,12 +94,16 @@ extern "C" bt_status bt_autotune(const void *h_keys, const void *h_vals, uint64_
         bool won = false;
         for (uint32_t w : warps)
             for (uint32_t p : pins)
-                for (uint32_t cfg = 0; cfg < 3; ++cfg) {
-                // (staging, queries per lane): (cp.async, 1), (bulk, 1), (cp.async, 2)
-                const uint32_t sm = cfg == 1 ? 1u : 0u, lq = cfg == 2 ? 2u : 1u;
+                for (uint32_t cfg = 0; cfg < 5; ++cfg) {
+                // (staging, queries per lane, inner levels staged): (pipelined, 1, L1),
+                // (pipelined, 1, staged), (cp.async, 1), (bulk, 1), (cp.async, 2)
+                static const uint32_t kStage[5] = {BT_STAGE_PIPELINED, BT_STAGE_PIPELINED, BT_STAGE_CP_ASYNC,
+                                                   BT_STAGE_BULK, BT_STAGE_CP_ASYNC};
+                const uint32_t sm = kStage[cfg], lq = cfg == 4 ? 2u : 1u, inner = cfg == 1 ? 1u : 0u;
                 bt_tree_set_launch(t, w, p);
                 bt_tree_set_staging(t, sm);
                 bt_tree_set_lane_queries(t, lq);
+                bt_tree_set_descent(t, inner, 0);
                 float us = 0;
                 st = time_search(t, d_sample, nsample, sc, ws_bytes, s, &us);
                 if (st != BT_OK) {
@@ -108,7 +112,7 @@ extern "C" bt_status bt_autotune(const void *h_keys, const void *h_vals, uint64_
                     return st;
                 }
                 if (b.fanout == 0 || us < b.us_per_batch) {
-                    b = bt_tune{m, w, p, sm, lq, us};
+                    b = bt_tune{m, w, p, sm, lq, inner, us};
                     won = true;
                 }
             }
@@ -122,6 +126,7 @@ extern "C" bt_status bt_autotune(const void *h_keys, const void *h_vals, uint64_
     bt_tree_set_launch(keep, b.warps_per_block, b.pin_bytes);
     bt_tree_set_staging(keep, b.staging);
     bt_tree_set_lane_queries(keep, b.lane_queries);
+    bt_tree_set_descent(keep, b.inner_staged, 0);
     *out = keep;
     *best = b;
     return BT_OK;

@@ -1,0 +1,121 @@
+"""The descent's selectable designs give the oracle's results, bit-exact:
+the pipelined descent (leaf blocks staged by bulk copies overlapped with
+the next chunk) with inner levels read through L1 or staged in shared
+memory, leaf ranks by binary search or by warp ballot + popc, with and
+without the L2 persistence window; the synchronous descents; and the
+bounded wait of the bulk-copy staging, made to give up on purpose."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from oracle import OracleTree
+from paper_2604_21117_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bt():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_21117_gb300 import build_lib
+    build_lib.build()
+    from paper_2604_21117_gb300 import btree
+    return btree
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _same(tree, o, q, sort_bits=-1):
+    v, f = tree.search(_dev(q), sort_bits=sort_bits)
+    ov, of, _, _ = o.search(q)
+    gv = v.cpu().numpy().astype(np.uint64)
+    gf = f.cpu().numpy()
+    bad = np.nonzero((gv != ov) | (gf != of))[0]
+    assert bad.size == 0, f"{bad.size} mismatches, first at {int(bad[0])}"
+
+
+@pytest.mark.parametrize("inner,ballot", [(0, 0), (1, 0), (0, 1), (1, 1)])
+@pytest.mark.parametrize("m", [8, 16, 32, 64])
+@pytest.mark.parametrize("kw,vw", [(32, 32), (64, 64), (64, 32)])
+def test_pipelined_options(bt, inner, ballot, m, kw, vw):
+    """Every fanout and width; sorted (auto, forced) and unsorted batches;
+    a ragged size, so the last chunk has tail lanes."""
+    keys = W.uniform_keys(90_000 + m, kw, seed=500 + m + kw)
+    vals = W.rank_values(keys.size, vw)
+    tree = bt.BTree(keys, vals, m)
+    bt.bt_tree_set_staging(tree.handle, bt.BT_STAGE_PIPELINED)
+    bt.bt_tree_set_descent(tree.handle, inner, ballot)
+    o = OracleTree(keys, vals, m, val_bits=vw)
+    q = W.make_queries(keys, 40_011, 0.8, seed=600 + m, width_bits=kw, zipf_s=1.1)
+    for sb in (-1, 0, 12):
+        _same(tree, o, q, sb)
+    bt.bt_check_timeouts()
+
+
+@pytest.mark.parametrize("staging", [0, 1, 2])
+@pytest.mark.parametrize("nq", [1, 31, 33, 1000, 16_384, 100_003])
+def test_staging_modes_and_sizes(bt, staging, nq):
+    keys = W.uniform_keys(400_000, 64, seed=610)
+    vals = W.rank_values(keys.size, 64)
+    tree = bt.BTree(keys, vals, 32)
+    bt.bt_tree_set_staging(tree.handle, staging)
+    o = OracleTree(keys, vals, 32)
+    q = W.make_queries(keys, nq, 0.9, seed=611 + nq, width_bits=64)
+    _same(tree, o, q)
+    bt.bt_check_timeouts()
+
+
+@pytest.mark.parametrize("warps,pin", [(4, 0), (8, 16384), (16, 49152)])
+def test_pipelined_launch_settings(bt, warps, pin):
+    keys = W.uniform_keys(700_000, 64, seed=620)
+    vals = W.rank_values(keys.size, 64)
+    tree = bt.BTree(keys, vals, 16)
+    bt.bt_tree_set_launch(tree.handle, warps, pin)
+    o = OracleTree(keys, vals, 16)
+    _same(tree, o, W.make_queries(keys, 70_001, 0.9, seed=621, width_bits=64))
+
+
+@pytest.mark.parametrize("m", [16, 32])
+def test_l2_window_keeps_results(bt, m):
+    keys = W.uniform_keys(2_000_000, 64, seed=630 + m)
+    vals = W.rank_values(keys.size, 64)
+    tree = bt.BTree(keys, vals, m)
+    o = OracleTree(keys, vals, m)
+    q = W.make_queries(keys, 200_000, 0.9, seed=631, width_bits=64)
+    bt.bt_tree_set_l2_window(tree.handle, 64 << 20)
+    _same(tree, o, q)
+    bt.bt_tree_set_l2_window(tree.handle, 0)
+    _same(tree, o, q)
+
+
+@pytest.mark.parametrize("staging", [1, 2])
+def test_bounded_wait_gives_up_and_is_reported(bt, staging):
+    """With the first wait's poll limit at 0 every bulk-copy wait gives up at
+    once: the warp counts it, waits (full limit) for its copies, and stops.
+    bt_check_timeouts reports it; with the limit restored the next search is
+    bit-exact and nothing more is reported."""
+    import torch
+    keys = W.uniform_keys(300_000, 64, seed=640)
+    vals = W.rank_values(keys.size, 64)
+    tree = bt.BTree(keys, vals, 32)
+    bt.bt_tree_set_staging(tree.handle, staging)
+    o = OracleTree(keys, vals, 32)
+    q = W.make_queries(keys, 50_000, 0.9, seed=641, width_bits=64)
+    bt.bt_check_timeouts()  # clear anything earlier
+    try:
+        bt.bt_debug_set_wait_polls(0)
+        tree.search(_dev(q))
+        torch.cuda.synchronize()
+    finally:
+        bt.bt_debug_set_wait_polls(bt.BT_DEFAULT_WAIT_POLLS)
+    with pytest.raises(bt.BTreeError) as e:
+        bt.bt_check_timeouts()
+    assert e.value.code == "BT_ERR_TIMEOUT"
+    _same(tree, o, q)
+    bt.bt_check_timeouts()  # nothing new

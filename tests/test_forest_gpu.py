@@ -104,7 +104,8 @@ def test_forest_search_replays_from_a_cuda_graph(bt):
 
 @pytest.mark.parametrize("warps,pin,staging,lq", [(4, 0, 0, 1), (16, 0, 0, 1), (4, 49152, 0, 1), (16, 49152, 0, 1),
                                                   (8, 16384, 0, 1), (4, 0, 1, 1), (16, 49152, 1, 1), (8, 16384, 1, 1),
-                                                  (8, 16384, 0, 2), (4, 0, 0, 2), (16, 49152, 0, 2)])
+                                                  (8, 16384, 0, 2), (4, 0, 0, 2), (16, 49152, 0, 2),
+                                                  (4, 0, 2, 1), (16, 49152, 2, 1), (8, 16384, 2, 1)])
 def test_launch_settings_do_not_change_results(bt, warps, pin, staging, lq):
     keys = W.uniform_keys(500_000, 64, seed=63)
     vals = W.rank_values(keys.size, 64)
@@ -146,7 +147,8 @@ def test_autotune_returns_a_correct_tree(bt):
     h, best = bt.bt_autotune(keys, vals, torch.from_numpy(sample).cuda(), sample.size)
     tree = bt.BTree(None, None, handle=h)
     assert best.fanout in (8, 16, 32, 64) and best.warps_per_block in (4, 8, 16)
-    assert best.pin_bytes in (0, 16384, 49152) and best.staging in (0, 1) and best.lane_queries in (1, 2)
+    assert best.pin_bytes in (0, 16384, 49152) and best.staging in (0, 1, 2) and best.lane_queries in (1, 2)
+    assert best.inner_staged in (0, 1)
     assert best.us_per_batch > 0
     assert tree.fanout == best.fanout
     o = OracleTree(keys, vals, best.fanout)

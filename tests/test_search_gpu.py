@@ -8,6 +8,7 @@ import pytest
 from paper_2604_21117_gb300 import workloads as W
 from oracle import OracleTree
 import pins
+import sortcheck
 
 pytestmark = pytest.mark.gpu
 
@@ -248,37 +249,33 @@ def _splitters(bt, tree):
 
 
 def _check_sort_contract(bt, tree, keys, q, hsq, hsi, sb):
-    """A permutation with its keys, ordered by a bucket number monotone in
-    the key: exactly ordered by splitter segment (the count of the tree's
-    splitters below the key), and inside a segment out of order only
-    between keys less than one interpolation bucket apart."""
+    """A permutation with its keys, in the documented order: by coarse
+    bucket, and inside coarse buckets of at most the tile size by the bucket
+    number f -- exactly by splitter segment (the count of the tree's
+    splitters below the key), inside a segment out of order only between keys
+    less than one interpolation bucket apart."""
     nq = q.size
     assert np.array_equal(np.sort(hsi), np.arange(nq, dtype=np.uint32))
     assert np.array_equal(hsq, q[hsi])
-    bits = sb if sb > 0 else ((min(max((nq).bit_length() - 5, 1), 13)) if (sb < 0 and nq >= 16384) else 0)
-    bits = min(bits, 13)
-    if bits <= 0 or keys.size == 0:
+    sp, nsplit = _splitters(bt, tree)
+    bits = bt.bt_sort_bits(tree.handle, nq, sb)
+    if bits == 0:
         assert np.array_equal(hsi, np.arange(nq, dtype=np.uint32))
         return
-    sp, nsplit = _splitters(bt, tree)
-    cbits = nsplit.bit_length()
-    r, cshift = max(bits - cbits, 0), max(cbits - bits, 0)
+    if sb > 0:
+        assert bits == min(sb, 21)
+    if sb < 0:
+        assert bits == 0 if nq < 16384 else bits > 9
     k = hsq.astype(np.uint64)
     c = np.searchsorted(sp, k, side="left")
-    assert np.all(np.diff(c >> cshift) >= 0)
-    if r == 0:
-        return
     lo = np.concatenate([[int(keys[0])], sp.astype(object)]) if nsplit else np.array([int(keys[0])], object)
     hi = np.concatenate([sp.astype(object), [int(keys[-1])]]) if nsplit else np.array([int(keys[-1])], object)
-    starts = np.flatnonzero(np.diff(c, prepend=-1))
-    ends = np.append(starts[1:], nq)
-    for s0, e0 in zip(starts, ends):
-        seg = int(c[s0])
-        bw = (int(hi[seg]) - int(lo[seg]) + 1) / (1 << r)
-        # keys beyond the key range share the end buckets
-        run = np.clip(k[s0:e0], np.uint64(keys[0]), np.uint64(keys[-1])).astype(np.float64)
-        back = np.maximum.accumulate(run) - run
-        assert back.max() <= bw * 1.01 + 2, (seg, back.max(), bw)
+    lo_f = np.array([float(x) for x in lo])
+    width = np.array([float(int(h) - int(l) + 1) for l, h in zip(lo, hi)])
+    # keys beyond the key range share the end buckets
+    run = np.clip(k, np.uint64(keys[0]), np.uint64(keys[-1])).astype(np.float64)
+    sortcheck.check_order(c, bits, nsplit, sortcheck.tile_for(int(keys.dtype.itemsize)),
+                          pos=run - lo_f[c], width=width[c])
 
 
 @pytest.mark.parametrize("kw", [32, 64])
