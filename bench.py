@@ -68,9 +68,9 @@ def parse_args(argv=None):
     p.add_argument("--staging", type=int, default=2,
                    help="descent: 2 = pipelined (bulk-copy leaf staging overlapped with the next chunk), "
                         "0 = synchronous 16-byte cp.async, 1 = synchronous bulk copy")
-    p.add_argument("--inner", type=int, default=0, help="pipelined: inner levels read through L1 (0) or staged (1)")
+    p.add_argument("--inner", type=int, default=1, help="pipelined: inner levels read through L1 (0) or staged (1)")
     p.add_argument("--ballot", type=int, default=0, help="pipelined: leaf rank by binary search (0) or ballot (1)")
-    p.add_argument("--l2-window", type=int, default=0,
+    p.add_argument("--l2-window", type=int, default=64 << 20,
                    help="bytes of the L2 persistence window on the inner levels (0 = none)")
     p.add_argument("--no-designs", action="store_true", help="skip the A/B of the descent designs")
     p.add_argument("--lane-queries", type=int, default=1, help="queries per lane of the descent (1 or 2)")
@@ -341,10 +341,10 @@ def cpu_baseline(keys, vals, m, q, budget_s: float = 12.0):
 # ------------------------------------------------------ designs leg
 
 DESIGNS = (
-    ("pipelined, inner through L1, binary search", dict(staging=2, inner=0, ballot=0, l2=0, lq=1)),
-    ("pipelined, inner through L1, ballot + popc", dict(staging=2, inner=0, ballot=1, l2=0, lq=1)),
-    ("pipelined, inner staged, binary search", dict(staging=2, inner=1, ballot=0, l2=0, lq=1)),
-    ("pipelined, inner through L1, L2 window", dict(staging=2, inner=0, ballot=0, l2=64 << 20, lq=1)),
+    ("pipelined, inner staged, binary search, L2 window", dict(staging=2, inner=1, ballot=0, l2=64 << 20, lq=1)),
+    ("pipelined, inner staged, ballot + popc, L2 window", dict(staging=2, inner=1, ballot=1, l2=64 << 20, lq=1)),
+    ("pipelined, inner through L1, binary search, L2 window", dict(staging=2, inner=0, ballot=0, l2=64 << 20, lq=1)),
+    ("pipelined, inner staged, binary search, no L2 window", dict(staging=2, inner=1, ballot=0, l2=0, lq=1)),
     ("synchronous cp.async (every level staged, waited)", dict(staging=0, inner=0, ballot=0, l2=0, lq=1)),
     ("synchronous bulk copy", dict(staging=1, inner=0, ballot=0, l2=0, lq=1)),
     ("synchronous, two queries per lane", dict(staging=0, inner=0, ballot=0, l2=0, lq=2)),
@@ -882,7 +882,7 @@ def run_ours(a):
     default_workload = (a.keys == 1 << 24 and a.batch == 1 << 20 and a.fanout == 32 and a.zipf is None
                         and abs(a.hit - 0.9) < 1e-9)
     if (NCU_DESCEND_TRAFFIC["descend_src_sha256"] == src_sha256() and default_workload and a.lane_queries == 1
-            and a.staging == 2 and a.inner == 0 and a.ballot == 0 and a.l2_window == 0 and a.warps <= 0
+            and a.staging == 2 and a.inner == 1 and a.ballot == 0 and a.l2_window == 64 << 20 and a.warps <= 0
             and a.pin < 0 and a.sort_bits < 0):
         traffic = NCU_DESCEND_TRAFFIC["bytes_per_launch"]
     step_gbs = statistics.fmean(node_bytes) / (statistics.fmean(step_ms) / 1e3) / 1e9

@@ -50,9 +50,15 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
+def _extra_flags():
+    """Extra nvcc flags from BT_NVCC_FLAGS (space-separated), for developers
+    comparing build-time variants; empty by default."""
+    return os.environ.get("BT_NVCC_FLAGS", "").split()
+
+
 def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
     """Compile and link the library; returns its path."""
-    if not force and up_to_date():
+    if not force and not _extra_flags() and up_to_date():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
@@ -61,7 +67,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     for src in _sources():
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
-        cmd = [cc, *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj]
+        cmd = [cc, *ARCH, *NVCC_FLAGS, *_extra_flags(), "-c", src, "-o", obj]
         if ptxas_info:
             cmd.insert(1, "-Xptxas=-v")
         if verbose:

@@ -338,6 +338,7 @@ extern "C" bt_status bt_build(const void *h_keys, const void *h_vals, uint64_t n
     d.warps = 8;
     d.lane_queries = 1;
     d.staging = BT_STAGE_PIPELINED;
+    d.inner_stage = 1;
     set_pin_levels(d, t->info, 16384);
 
     // Shape arithmetic: children (or keys, for leaves) per node.

@@ -32,6 +32,20 @@
 
 #include "descent.cuh"
 
+// Leaf blocks and values are loaded with an L2 evict-first policy (1), or
+// with the default policy (0).
+#ifndef BT_LEAF_EVICT_FIRST
+#define BT_LEAF_EVICT_FIRST 1
+#endif
+// Register limit of the pipelined descent (0: the compiler's choice).
+#ifndef BT_DESCEND_MAXNREG
+#define BT_DESCEND_MAXNREG 0
+#endif
+// Inner-level slots per warp when inner levels are staged.
+#ifndef BT_INNER_SLOTS
+#define BT_INNER_SLOTS 4
+#endif
+
 namespace btgb {
 
 // Leaf blocks a warp stages per round (about 4 KB), and inner-level slots.
@@ -47,7 +61,7 @@ constexpr int leaf_slots()
 template <typename K, int M>
 constexpr int inner_slots()
 {
-    return leaf_slots<K, M>() / 4 > 0 ? leaf_slots<K, M>() / 4 : 1;
+    return leaf_slots<K, M>() * BT_INNER_SLOTS / 16 > 0 ? leaf_slots<K, M>() * BT_INNER_SLOTS / 16 : 1;
 }
 
 template <typename K, int M, bool LEARN>
@@ -69,7 +83,28 @@ __device__ __forceinline__ void issue_leaf_round(K *stage, const K *lk, const ui
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (lane == 0) mbar_arrive_expect_tx(mbar, static_cast<unsigned>(nu) * kBlk);
     __syncwarp();
-    if (lane < nu) bulk_g2s(stage + lane * M, lk + static_cast<uint64_t>(lst[lane]) * M, kBlk, mbar);
+    if (lane < nu) {
+#if BT_LEAF_EVICT_FIRST
+        bulk_g2s_hint(stage + lane * M, lk + static_cast<uint64_t>(lst[lane]) * M, kBlk, mbar, l2_evict_first_policy());
+#else
+        bulk_g2s(stage + lane * M, lk + static_cast<uint64_t>(lst[lane]) * M, kBlk, mbar);
+#endif
+    }
+}
+
+// A leaf value, read once.
+template <typename V>
+__device__ __forceinline__ V ld_value(const V *p)
+{
+#if BT_LEAF_EVICT_FIRST
+    if constexpr (sizeof(V) == 8) {
+        return static_cast<V>(__ldcs(reinterpret_cast<const unsigned long long *>(p)));
+    } else {
+        return static_cast<V>(__ldcs(reinterpret_cast<const unsigned int *>(p)));
+    }
+#else
+    return *p;
+#endif
 }
 
 // Rank (and equality) of each lane's key in its leaf, for the lanes whose
@@ -108,8 +143,14 @@ __device__ __forceinline__ void leaf_rank_round(const K *stage, int rb, int nu, 
     }
 }
 
+#if BT_DESCEND_MAXNREG
+#define BT_DESCEND_REGS __maxnreg__(BT_DESCEND_MAXNREG)
+#else
+#define BT_DESCEND_REGS __launch_bounds__(kDescWarpsMax * 32)
+#endif
+
 template <typename K, typename V, int M, bool COUNT, bool LEARN>
-__global__ void __launch_bounds__(kDescWarpsMax * 32) k_descend(
+__global__ void BT_DESCEND_REGS k_descend(
     const DevTree t, const RawOf<K> *__restrict__ q, const uint32_t *__restrict__ qidx,
     const PartRec<K> *__restrict__ recs, uint64_t nq, V *__restrict__ out_v, uint8_t *__restrict__ out_f,
     unsigned long long *__restrict__ fetch, const ModelDev md,
@@ -175,6 +216,8 @@ __global__ void __launch_bounds__(kDescWarpsMax * 32) k_descend(
     }
     cp_async_wait_all();
     __syncthreads();
+    // the batch (and the outputs) belong to the previous kernel until it is done
+    pdl_wait();
 
     const uint64_t nchunks = (nq + 31) / 32;
     const uint64_t stride = static_cast<uint64_t>(gridDim.x) * nw;
@@ -348,7 +391,7 @@ __global__ void __launch_bounds__(kDescWarpsMax * 32) k_descend(
             const uint64_t cnt = t.cbase[LEAF] + (a_node < t.crem[LEAF] ? 1u : 0u);
             const bool hit = (static_cast<uint64_t>(r) < cnt) && eq;
             pend_val = static_cast<V>(~static_cast<V>(0));
-            if (hit) pend_val = vals[static_cast<uint64_t>(a_node) * M + r];
+            if (hit) pend_val = ld_value(vals + static_cast<uint64_t>(a_node) * M + r);
             pend_hit = hit;
             pend_dst = a_dst;
             pend_store = a_valid && a_dst < nq;  // a position outside the batch is never written
@@ -377,8 +420,9 @@ __global__ void __launch_bounds__(kDescWarpsMax * 32) k_descend(
     }
 }
 
-// Launch through cudaLaunchKernelEx, with the tree's L2 access-policy
-// window (the non-pinned inner levels marked persisting) when it has one.
+// Launch through cudaLaunchKernelEx as a programmatic dependent launch, with
+// the tree's L2 access-policy window (the non-pinned inner levels marked
+// persisting) when it has one.
 template <typename... KArgs, typename... Args>
 static cudaError_t launch_with_window(void (*kern)(KArgs...), unsigned grid, int threads, int smem, cudaStream_t s,
                                       const bt_tree *tree, Args... args)
@@ -389,18 +433,24 @@ static cudaError_t launch_with_window(void (*kern)(KArgs...), unsigned grid, int
     cfg.blockDim = dim3(static_cast<unsigned>(threads));
     cfg.dynamicSmemBytes = static_cast<size_t>(smem);
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
+    memset(attr, 0, sizeof(attr));
+    // may start while the previous kernel finishes (the kernel waits for it,
+    // pdl_wait, before touching the batch or the outputs)
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    unsigned n = 1;
     if (tree && tree->l2_bytes) {
-        memset(attr, 0, sizeof(attr));
-        attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
-        attr[0].val.accessPolicyWindow.base_ptr = const_cast<void *>(tree->l2_base);
-        attr[0].val.accessPolicyWindow.num_bytes = static_cast<size_t>(tree->l2_bytes);
-        attr[0].val.accessPolicyWindow.hitRatio = tree->l2_hit_ratio;
-        attr[0].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
-        attr[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
+        attr[1].id = cudaLaunchAttributeAccessPolicyWindow;
+        attr[1].val.accessPolicyWindow.base_ptr = const_cast<void *>(tree->l2_base);
+        attr[1].val.accessPolicyWindow.num_bytes = static_cast<size_t>(tree->l2_bytes);
+        attr[1].val.accessPolicyWindow.hitRatio = tree->l2_hit_ratio;
+        attr[1].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+        attr[1].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+        n = 2;
     }
+    cfg.attrs = attr;
+    cfg.numAttrs = n;
     return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 

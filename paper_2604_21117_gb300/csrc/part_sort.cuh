@@ -520,6 +520,9 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_partition(const RawOf<K> *_
         if (threadIdx.x == 0) atomicAdd(&g_part_timeouts, 1u);
         return;
     }
+    // the next kernel (the descent) may start launching; it waits for this
+    // grid to finish before it reads the records
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     // 5. local sorts, in place: the block's threads form kSortGroups groups
     // of kSortThreads, each ordering one coarse bucket of at most part_tile
     // records at a time by digit (records in registers, ranks among equal
