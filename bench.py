@@ -101,7 +101,8 @@ def workload_config(a, world: int) -> dict:
             "l2": ("GPU arm: not flushed between steps (the 282 MB tree exceeds the 129 MB L2; batches "
                    "rotate); a 256 MB write-flushed loop is reported beside it" if a.l2 == "none" else
                    f"GPU arm: L2 {a.l2}-flushed (256 MB) before every timed step"),
-            "parallelism": "replicas" if world > 1 else "single GPU"}
+            "parallelism": (f"replicas: one batch of {world} x {a.batch} queries split evenly over {world} GPUs, "
+                            "each holding the whole tree" if world > 1 else "single GPU")}
 
 
 def make_tree_data(a):
@@ -110,9 +111,18 @@ def make_tree_data(a):
     return keys, vals
 
 
-def make_batches(a, keys, count: int, rank: int = 0):
-    return [W.make_queries(keys, a.batch, a.hit, seed=W.SEED_BASE + 2 + 1000 * (i + 1) + 7919 * rank,
-                           width_bits=64, zipf_s=a.zipf) for i in range(count)]
+def make_batches(a, keys, count: int, rank: int = 0, world: int = 1):
+    """`count` batches of a.batch queries for this rank.  With several ranks
+    every rank draws the same global batch of world * a.batch queries and
+    takes its even slice of it (the replicas' split of one batch)."""
+    from paper_2604_21117_gb300.replicas import even_slice
+    out = []
+    for i in range(count):
+        g = W.make_queries(keys, a.batch * world, a.hit, seed=W.SEED_BASE + 2 + 1000 * (i + 1), width_bits=64,
+                           zipf_s=a.zipf)
+        s, c = even_slice(g.size, world, rank)
+        out.append(np.ascontiguousarray(g[s:s + c]))
+    return out
 
 
 def level_node_max(keys: np.ndarray, level_nodes: list[int]) -> list[np.ndarray]:
@@ -307,35 +317,59 @@ def barrier(world: int):
 
 # ---------------------------------------------------------- CPU oracle
 
-def cpu_baseline(keys, vals, m, q, budget_s: float = 12.0):
-    """Time the CPU oracle (pointer B+ tree, one query at a time) on a
-    bounded sample of the batch: single thread and all host cores."""
+CPU_SAMPLE = 1 << 16  # queries per CPU-oracle repeat, in both arms
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (or its implementer/part codes on Arm)."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            info = f.read()
+    except OSError:
+        return "unknown"
+    for line in info.splitlines():
+        if line.lower().startswith(("model name", "hardware")):
+            return line.split(":", 1)[1].strip()
+    imp = part = None
+    for line in info.splitlines():
+        if line.startswith("CPU implementer"):
+            imp = line.split(":", 1)[1].strip()
+        elif line.startswith("CPU part"):
+            part = line.split(":", 1)[1].strip()
+    return f"Arm implementer {imp}, part {part}" if imp else "unknown"
+
+
+def cpu_baseline(keys, vals, m, q, repeats: int = 100):
+    """The CPU oracle (pointer B+ tree, each query descending from the root)
+    on the first CPU_SAMPLE queries of a batch, split evenly over T threads
+    for T in {1, 2, 4, 8, 16, all cores}; every T timed `repeats` times and
+    summarised by the IQM (the paper's Eq. 2) and the interquartile range,
+    as the paper's 1- and 16-thread CPU comparison (Sec. V-C, V-F)."""
     import oracle
     t0 = time.perf_counter()
     tree = oracle.OracleTree(keys, vals, m)
     build_s = time.perf_counter() - t0
     cores = os.cpu_count() or 1
-    probe = q[: min(q.size, 1 << 14)]
-    t0 = time.perf_counter()
-    tree.search(probe)
-    per_q = (time.perf_counter() - t0) / probe.size
-    n1 = int(min(q.size, max(1 << 14, (budget_s * 0.4) / max(per_q, 1e-9))))
-    t0 = time.perf_counter()
-    tree.search_mt(q[:n1], 1)
-    t1 = time.perf_counter() - t0
-    nm = int(min(q.size, max(1 << 16, (budget_s * 0.4) * cores / max(per_q, 1e-9))))
-    reps = []
-    for _ in range(3):
-        t0 = time.perf_counter()
-        tree.search_mt(q[:nm], cores)
-        reps.append(time.perf_counter() - t0)
-    tm = iqm(reps)
+    sample = q[: min(q.size, CPU_SAMPLE)]
+    threads = sorted({1, 2, 4, 8, 16, cores} & set(range(1, cores + 1)) | {cores})
+    table = {}
+    for T in threads:
+        tree.search_mt(sample, T)  # warm-up
+        ts = []
+        for _ in range(repeats):
+            t1 = time.perf_counter()
+            tree.search_mt(sample, T)
+            ts.append(time.perf_counter() - t1)
+        q25, q75 = np.percentile(ts, [25, 75])
+        table[str(T)] = {"lookups_per_s": sample.size / iqm(ts), "iqm_ms": 1e3 * iqm(ts),
+                         "iqr_ms": 1e3 * float(q75 - q25)}
     tree.close()
-    return {"value": nm / tm, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "value_1thread": n1 / t1,
-            "sample": (f"first {nm} queries of one batch on {cores} threads (batch split evenly), "
-                       f"IQM of 3 runs; 1-thread figure on the first {n1}; oracle tree build "
-                       f"{build_s:.1f} s untimed")}
+    return {"value": table[str(cores)]["lookups_per_s"], "unit": UNIT, "cores": cores, "kind": "oracle",
+            "value_1thread": table["1"]["lookups_per_s"], "threads": table,
+            "cpu_model": cpu_model(), "hardware_concurrency": cores,
+            "sample": (f"the first {sample.size} queries of one batch, split evenly over T threads; "
+                       f"{repeats} repeats per T, IQM (Eq. 2) and IQR; oracle tree build {build_s:.1f} s "
+                       "untimed; value = all cores")}
 
 
 # ------------------------------------------------------ designs leg
@@ -792,7 +826,7 @@ def run_ours(a):
 
     keys, vals = make_tree_data(a)
     pool = 4
-    batches = make_batches(a, keys, pool, rank)
+    batches = make_batches(a, keys, pool, rank, world)
     tree = bt.BTree(keys, vals, a.fanout)
     bt.bt_tree_set_staging(tree.handle, a.staging)
     bt.bt_tree_set_lane_queries(tree.handle, a.lane_queries)
@@ -866,9 +900,20 @@ def run_ours(a):
     value = B * K * world / total_s_max
 
     # correctness spot check of the last step against the plain definition
-    last = batches[(K - 1) % pool]
-    got_v = out_v.cpu().numpy()
-    got_f = out_f.cpu().numpy()
+    if world > 1:
+        # the ranks' results of the last batch, reassembled in input order
+        from paper_2604_21117_gb300.replicas import gather_in_input_order
+        gv = gather_in_input_order(out_v.view(torch.int64), B * world, world, rank)
+        gf = gather_in_input_order(out_f.to(torch.int64), B * world, world, rank)
+        got_v = gv.cpu().numpy().view(np.uint64)
+        got_f = gf.cpu().numpy().astype(np.uint8)
+        i_last = (K - 1) % pool
+        last = W.make_queries(keys, B * world, a.hit, seed=W.SEED_BASE + 2 + 1000 * (i_last + 1), width_bits=64,
+                              zipf_s=a.zipf)
+    else:
+        last = batches[(K - 1) % pool]
+        got_v = out_v.cpu().numpy()
+        got_f = out_f.cpu().numpy()
     pos = np.searchsorted(keys, last)
     hit = (pos < keys.size) & (keys[np.minimum(pos, keys.size - 1)] == last)
     ok = bool(np.array_equal(got_f.astype(bool), hit) and np.array_equal(got_v[hit], vals[pos[hit]]))
@@ -1080,7 +1125,7 @@ def run_reference(a):
     q = make_batches(a, keys, 1)[0]
     tree = oracle.OracleTree(keys, vals, a.fanout)
     cores = os.cpu_count() or 1
-    sample = min(q.size, 1 << 16)
+    sample = min(q.size, CPU_SAMPLE)
     qs = q[:sample]
     for _ in range(a.warmup):
         tree.search_mt(qs, cores)
@@ -1098,8 +1143,9 @@ def run_reference(a):
         "data": "synthetic (seeded uniform keys and query mix)",
         "config": workload_config(a, world),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"each step: the first {sample} queries of the batch, split evenly "
-                                   f"over {cores} threads"},
+                         "cpu_model": cpu_model(), "hardware_concurrency": cores,
+                         "sample": f"each step: the first {sample} queries of the batch (the same sample as "
+                                   f"the GPU arm's cpu_baseline), split evenly over {cores} threads"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     tree.close()

@@ -545,7 +545,8 @@ typedef struct bt_server_stats {
 
 /* Start a server over `ntrees` resident trees (equal key and value widths).
  * models: NULL, or one entry per tree, NULL or a model trained on that tree
- * (its searches then use bt_learned_search_batch).  Trees and models must
+ * (its searches then use bt_learned_search_batch; a model for an empty tree
+ * is BT_ERR_ARG).  Trees and models must
  * outlive the server.  Allocates the slots' buffers and starts the worker on
  * the current device.  Errors: BT_ERR_ARG, BT_ERR_NOMEM, BT_ERR_CUDA. */
 bt_status bt_server_create(const bt_tree *const *trees, const bt_model *const *models, uint32_t ntrees,
@@ -554,7 +555,11 @@ bt_status bt_server_create(const bt_tree *const *trees, const bt_model *const *m
 /* Queue one request of `count` keys (host memory, read when its batch is
  * formed) for tree number `tree`; the results are written to h_out_vals /
  * h_out_found (host) before the request's ticket is reported done.  Buffers
- * must stay valid until then.  Thread-safe.  BT_ERR_NOMEM: pending cap. */
+ * must stay valid until then.  Thread-safe.  BT_ERR_NOMEM: the pending cap
+ * is full now (retry later); BT_ERR_ARG: count is 0 or above max_batch, or
+ * the request alone exceeds pending_cap_bytes.  If a batch cannot be issued
+ * (a failing CUDA call), its requests are never reported done and every
+ * later call returns the error. */
 bt_status bt_server_submit(bt_server *server, uint32_t tree, const void *h_keys, uint32_t count,
                            void *h_out_vals, uint8_t *h_out_found, uint64_t *ticket);
 

@@ -76,6 +76,7 @@ struct bt_server {
     std::vector<uint64_t> done_tickets;
     std::vector<float> latencies;  // per completed request, us
     uint64_t completed = 0, lookups = 0, batches = 0, submitted = 0;
+    uint64_t failed = 0;  // requests of batches that could not be issued
     uint32_t max_inflight_seen = 0;
     std::atomic<bool> stop{false};
     std::thread worker;
@@ -203,8 +204,16 @@ bool issue(bt_server *S)
     if (e == cudaSuccess && st == BT_OK) e = cudaMemcpyAsync(sl.h_f, sl.d_f, off, cudaMemcpyDeviceToHost, sl.stream);
     if (e == cudaSuccess && st == BT_OK) e = cudaEventRecord(sl.done, sl.stream);
     if (e != cudaSuccess || st != BT_OK) {
+        // the batch never ran: its requests are not reported done (the
+        // server's status, returned by every later call, says why), and no
+        // results are copied into their buffers
         if (e != cudaSuccess) btgb::set_error_detail("server issue", e);
+        std::lock_guard<std::mutex> lk(S->mu);
         S->worker_status = st != BT_OK ? st : BT_ERR_CUDA;
+        S->failed += sl.reqs.size();
+        S->inflight_bytes -= sl.bytes;
+        sl.reqs.clear();
+        return true;
     }
     sl.busy = true;
     return true;
@@ -262,7 +271,8 @@ extern "C" bt_status bt_server_create(const bt_tree *const *trees, const bt_mode
         if (!trees[i] || trees[i]->dev.key_bytes != trees[0]->dev.key_bytes ||
             trees[i]->dev.val_bytes != trees[0]->dev.val_bytes)
             return BT_ERR_ARG;
-        if (models && models[i] && models[i]->dev.leaves != trees[i]->dev.nodes[trees[i]->dev.height - 1])
+        if (models && models[i] &&
+            (trees[i]->dev.height == 0 || models[i]->dev.leaves != trees[i]->dev.nodes[trees[i]->dev.height - 1]))
             return BT_ERR_ARG;
     }
     bt_server *S = new (std::nothrow) bt_server;
@@ -310,6 +320,8 @@ extern "C" bt_status bt_server_submit(bt_server *S, uint32_t tree, const void *h
     if (!S || tree >= S->trees.size() || count == 0 || !h_keys || !h_out_vals || !h_out_found) return BT_ERR_ARG;
     if (count > S->opts.max_batch) return BT_ERR_ARG;
     const uint64_t b = req_bytes(S, count);
+    // a request larger than the pending cap could never be admitted
+    if (S->opts.pending_cap_bytes && b > S->opts.pending_cap_bytes) return BT_ERR_ARG;
     std::lock_guard<std::mutex> lk(S->mu);
     if (S->worker_status != BT_OK) return S->worker_status;
     if (S->opts.pending_cap_bytes && S->pending_bytes + b > S->opts.pending_cap_bytes) return BT_ERR_NOMEM;
@@ -340,7 +352,7 @@ extern "C" bt_status bt_server_drain(bt_server *S, double timeout_s)
         {
             std::lock_guard<std::mutex> lk(S->mu);
             if (S->worker_status != BT_OK) return S->worker_status;
-            if (S->completed == S->submitted) return BT_OK;
+            if (S->completed + S->failed == S->submitted) return BT_OK;
         }
         if (now_us() > t_end) return BT_ERR_TIMEOUT;
         std::this_thread::sleep_for(std::chrono::microseconds(20));

@@ -90,3 +90,62 @@ def test_reduce_max_over_two_gloo_ranks():
     port = _free_port()
     mp.start_processes(_rank_main, args=(2, port, out), nprocs=2, start_method="spawn")
     assert dict(out) == {0: 2.5, 1: 2.5}
+
+
+@pytest.mark.parametrize("nq,world", [(0, 2), (1, 2), (7, 2), (10, 3), (1 << 20, 8), (1000003, 4)])
+def test_even_slices_cover_the_batch_once(nq, world):
+    from paper_2604_21117_gb300.replicas import even_slice
+    slices = [even_slice(nq, world, r) for r in range(world)]
+    assert sum(c for _, c in slices) == nq
+    assert max(c for _, c in slices) - min(c for _, c in slices) <= 1
+    pos = 0
+    for s, c in slices:  # contiguous, in rank order
+        assert s == pos
+        pos += c
+
+
+def _split_rank_main(rank, world, port, nq, out):
+    """Each rank searches its even slice of one batch with the CPU oracle and
+    the results are gathered back in input order."""
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    import torch
+    import torch.distributed as dist
+    from paper_2604_21117_gb300.replicas import even_slice, gather_in_input_order
+    bench.dist_init(world, "gloo")
+    keys = W.uniform_keys(50_000, 64, seed=90)
+    vals = W.rank_values(keys.size, 64)
+    q = W.make_queries(keys, nq, 0.8, seed=91, width_bits=64)
+    s, c = even_slice(nq, world, rank)
+    o = OracleTree(keys, vals, 16)
+    v, f, _, _ = o.search(q[s:s + c])
+    o.close()
+    gv = gather_in_input_order(torch.from_numpy(v.view(np.int64).copy()), nq, world, rank)
+    gf = gather_in_input_order(torch.from_numpy(f.astype(np.int64)), nq, world, rank)
+    out[rank] = (gv.numpy().view(np.uint64).tobytes(), gf.numpy().astype(np.uint8).tobytes())
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("nq", [1, 5_001])
+def test_batch_split_over_two_gloo_ranks(nq):
+    import torch.multiprocessing as mp
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_split_rank_main, args=(2, _free_port(), nq, out), nprocs=2, start_method="spawn")
+    keys = W.uniform_keys(50_000, 64, seed=90)
+    vals = W.rank_values(keys.size, 64)
+    q = W.make_queries(keys, nq, 0.8, seed=91, width_bits=64)
+    ev, ef = pins_lookup(keys, vals, q)
+    for r in range(2):
+        gv = np.frombuffer(out[r][0], np.uint64)
+        gf = np.frombuffer(out[r][1], np.uint8)
+        assert np.array_equal(gv, ev) and np.array_equal(gf, ef)
+
+
+def pins_lookup(keys, vals, q):
+    """The plain definition of a lookup (lower_bound on the sorted keys)."""
+    pos = np.searchsorted(keys, q)
+    hit = (pos < keys.size) & (keys[np.minimum(pos, keys.size - 1)] == q)
+    v = np.full(q.size, np.uint64(2**64 - 1))
+    v[hit] = vals[pos[hit]]
+    return v, hit.astype(np.uint8)
