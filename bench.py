@@ -68,7 +68,8 @@ def parse_args(argv=None):
     p.add_argument("--staging", type=int, default=2,
                    help="descent: 2 = pipelined (bulk-copy leaf staging overlapped with the next chunk), "
                         "0 = synchronous 16-byte cp.async, 1 = synchronous bulk copy")
-    p.add_argument("--inner", type=int, default=1, help="pipelined: inner levels read through L1 (0) or staged (1)")
+    p.add_argument("--inner", type=int, default=2,
+                   help="pipelined: inner levels through L1 (0), staged (1), staged only for partitioned batches (2)")
     p.add_argument("--ballot", type=int, default=0, help="pipelined: leaf rank by binary search (0) or ballot (1)")
     p.add_argument("--l2-window", type=int, default=64 << 20,
                    help="bytes of the L2 persistence window on the inner levels (0 = none)")
@@ -927,7 +928,7 @@ def run_ours(a):
     default_workload = (a.keys == 1 << 24 and a.batch == 1 << 20 and a.fanout == 32 and a.zipf is None
                         and abs(a.hit - 0.9) < 1e-9)
     if (NCU_DESCEND_TRAFFIC["descend_src_sha256"] == src_sha256() and default_workload and a.lane_queries == 1
-            and a.staging == 2 and a.inner == 1 and a.ballot == 0 and a.l2_window == 64 << 20 and a.warps <= 0
+            and a.staging == 2 and a.inner in (1, 2) and a.ballot == 0 and a.l2_window == 64 << 20 and a.warps <= 0
             and a.pin < 0 and a.sort_bits < 0):
         traffic = NCU_DESCEND_TRAFFIC["bytes_per_launch"]
     step_gbs = statistics.fmean(node_bytes) / (statistics.fmean(step_ms) / 1e3) / 1e9
@@ -945,7 +946,8 @@ def run_ours(a):
         "launch": {"sort_bits": "auto" if sort_bits < 0 else sort_bits,
                    "staging": {0: "synchronous cp.async", 1: "synchronous bulk copy",
                                2: "pipelined bulk-copy leaves"}[a.staging],
-                   "inner_levels": "staged (cp.async)" if a.inner else "through L1",
+                   "inner_levels": {0: "through L1", 1: "staged (cp.async)",
+                                    2: "staged (cp.async) for partitioned batches, else through L1"}[a.inner],
                    "leaf_rank": "ballot + popc" if a.ballot else "binary search",
                    "l2_window_bytes": a.l2_window, "lane_queries": a.lane_queries,
                    "l2": {"write": "flushed before every timed step (256 MB device write)",

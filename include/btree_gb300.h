@@ -412,16 +412,19 @@ bt_status bt_tree_set_staging(bt_tree *tree, uint32_t mode);
 
 /* Two choices of the pipelined descent (no counterpart in the paper beyond
  * Sec. IV-E's comparator row, which rank_ballot = 1 follows):
- *   inner_staged  0 (default): each lane reads its inner-level node block
- *                 through L1 (every 128-byte line of the block prefetched
- *                 first; lanes that share a node share its lines);
+ *   inner_staged  0: each lane reads its inner-level node block through L1
+ *                 (every 128-byte line of the block prefetched first; lanes
+ *                 that share a node share its lines);
  *                 1: each distinct inner node block is staged into shared
- *                 memory once with 16-byte cp.async, then searched there.
+ *                 memory once with 16-byte cp.async, then searched there;
+ *                 2 (default): 1 for partitioned batches (a warp meets one or
+ *                 two nodes per level), 0 for unsorted ones (up to 32).
  *   rank_ballot   0 (default): each query finds its leaf rank by binary
  *                 search in the staged block; 1: the rank is the population
  *                 count of a warp ballot, lane j comparing slot j (and j+32)
  *                 of the query's leaf, one query after another.
- * Results are identical; speed differs.  BT_ERR_ARG on values above 1. */
+ * Results are identical; speed differs.  BT_ERR_ARG on inner_staged above 2
+ * or rank_ballot above 1. */
 bt_status bt_tree_set_descent(bt_tree *tree, uint32_t inner_staged, uint32_t rank_ballot);
 
 /* An L2 access-policy window for the tree's searches: the inner levels below
@@ -472,6 +475,53 @@ bt_status bt_check_timeouts(void);
  */
 bt_status bt_autotune(const void *h_keys, const void *h_vals, uint64_t n, bt_width key_w, bt_width val_w,
                       const void *d_sample, uint64_t nsample, bt_stream stream, bt_tree **out, bt_tune *best);
+
+/* ------------------------------------------------------------------------
+ * Range-partitioned trees.  The paper runs several kernel instances on one
+ * batch (Sec. IV-G), each holding the whole tree; split by key range instead,
+ * each holds one part: P subtrees over contiguous key ranges, every query
+ * routed to the part whose range holds it and every result routed back to
+ * its input position.  Across GPUs each part lives on its own GPU and the
+ * routing is an exchange of queries and one of results
+ * (paper_2604_21117_gb300/range_split.py holds that host-side exchange); on
+ * one GPU, bt_range_search does both routings itself.
+ * ------------------------------------------------------------------------ */
+typedef struct bt_range bt_range;
+
+/*
+ * bt_range_build -- P = `parts` subtrees (1..64) over n sorted keys
+ * (integer keys only): part p holds the keys of rank floor(p n / P) ..
+ * floor((p+1) n / P) - 1 with their values, built with bt_build at `fanout`;
+ * splitter p (p < P - 1) is the largest key of part p.  n must be >= P.
+ * Synchronizes `stream`.  Errors: as bt_build, BT_ERR_ARG for P or n out of
+ * range or 32-byte keys.
+ */
+bt_status bt_range_build(const void *h_keys, const void *h_vals, uint64_t n, bt_width key_w, bt_width val_w,
+                         uint32_t fanout, uint32_t parts, bt_stream stream, bt_range **out);
+void bt_range_free(bt_range *range);
+
+/* The number of parts; optionally (non-NULL) the P - 1 splitters (as
+ * uint64) and the number of keys of every part.  BT_ERR_ARG on nulls. */
+bt_status bt_range_info(const bt_range *range, uint32_t *parts, uint64_t *h_splitters, uint64_t *h_part_keys);
+
+/* Part p's tree (owned by the range; NULL if p is out of range). */
+const bt_tree *bt_range_part(const bt_range *range, uint32_t p);
+
+/* Device workspace of bt_range_search for nq queries. */
+uint64_t bt_range_workspace_bytes(const bt_range *range, uint64_t nq);
+
+/*
+ * bt_range_search -- point lookups over the range-partitioned key set,
+ * results in input order (as bt_search_batch over all the keys).  Every query
+ * goes to the first part whose splitter is >= the query (the last part when
+ * none is); each part's queries are searched with bt_search_batch on that
+ * part's tree; results return to their input positions.  Reads the part
+ * sizes back to the host once (it synchronizes `stream`).  Not thread-safe
+ * for one range (the part sizes are staged in the range).
+ * Errors: as bt_search_batch.
+ */
+bt_status bt_range_search(const bt_range *range, const void *d_queries, uint64_t nq, void *d_out_vals,
+                          uint8_t *d_out_found, void *d_workspace, uint64_t ws_bytes, bt_stream stream);
 
 /* ------------------------------------------------------------------------
  * The paper's node layout (Sec. IV-B, Eq. 1, Fig. 3), for comparison with
@@ -603,11 +653,14 @@ bt_status bt_server_run_trace(bt_server *server, uint64_t n, const double *t_arr
  *                one past the largest key); a least-squares line per segment
  *                fitted in fp64 and stored in fp32; pred = fp32(fp32(slope_s *
  *                x) + icpt_s), separately rounded.
- *   BT_MODEL_MLP 1 -> 32 -> 32 -> 1 with ReLU on x = fp32(fp64(clamp(q) -
- *                kmin)) * fp32(1/fp64(kmax - kmin)); trained with Adam on the
- *                mean squared error against leaf / (L - 1); pred = output *
- *                (L - 1).  Parameters (BT_MLP_PARAMS floats): W1[32], b1[32],
- *                W2[32][32] (row = output unit), b2[32], w3[32], b3.
+ *   BT_MODEL_MLP 1 -> 32 -> 32 -> 1 with ReLU on a rank coordinate (two
+ *                stages): the first stage is 64 breakpoints b_s at key
+ *                quantiles with inv_w_s as for PL; x = fp32(fp32(s) +
+ *                min(fp32(fp64(q - b_s)) * inv_w_s, 1)) * (1/64), which follows
+ *                the key's rank whatever the key distribution; trained with
+ *                Adam on the mean squared error against leaf / (L - 1); pred =
+ *                output * (L - 1).  Parameters (BT_MLP_PARAMS floats): W1[32],
+ *                b1[32], W2[32][32] (row = output unit), b2[32], w3[32], b3.
  *   leaf_hat = rint(clamp(pred, 0, L - 1)).
  * ------------------------------------------------------------------------ */
 #define BT_MLP_PARAMS 1153

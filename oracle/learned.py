@@ -9,8 +9,10 @@ kernels can be checked:
   (the leaf index is the tree's own output, see OracleTree.search);
 * PL model: S segments split at key quantiles b_s = k[floor(s*n/S)], a
   least-squares line per segment on x = fp32(fp64(q - b_s)) * inv_w_s;
-* MLP model 1 -> 32 -> 32 -> 1 with ReLU on x = fp32(fp64(q - kmin)) *
-  inv_range, trained on the target leaf / (L - 1) with mean squared error;
+* MLP model 1 -> 32 -> 32 -> 1 with ReLU on a rank coordinate (two stages):
+  the first stage is 64 breakpoints at key quantiles, as the PL model's, and
+  x = fp32(fp32(s) + min(fp32(fp64(q - b_s)) * inv_w_s, 1)) * (1/64); trained
+  on the target leaf / (L - 1) with mean squared error;
 * prediction leaf_hat = rint(clamp(pred)) decided in fp32 exactly as the GPU
   does (separately rounded multiply and add for PL);
 * max_err = max over stored keys of |leaf_hat - leaf|.
@@ -141,11 +143,23 @@ def mlp_grad(p, x, t):
     return np.concatenate([g_W1, g_b1, g_W2.ravel(), g_b2, g_w3, [g_b3]])
 
 
-def mlp_x(keys_or_q, kmin: int, kmax: int):
-    """fp32(fp64(clamp(q) - kmin)) * inv_range, inv_range = fp32(1/fp64(kmax-kmin))."""
-    q = np.clip(np.asarray(keys_or_q).astype(np.uint64), np.uint64(kmin), np.uint64(kmax))
-    inv = np.float32(1.0 / float(kmax - kmin)) if kmax > kmin else np.float32(0.0)
-    return ((q - np.uint64(kmin)).astype(np.float64).astype(np.float32) * inv).astype(np.float32)
+MLP_STAGE1 = 64  # breakpoints of the MLP's first stage
+
+
+def mlp_stage1(keys: np.ndarray):
+    """The first stage's breakpoints: the PL breakpoints of 64 segments."""
+    return pl_breakpoints(keys, MLP_STAGE1)
+
+
+def mlp_x(keys_or_q, b, inv_w):
+    """The MLP's input, in fp32 as the GPU computes it: segment s of q among
+    the first stage's breakpoints, u = min(fp32(fp64(q - b_s)) * inv_w_s, 1),
+    x = fp32(fp32(s) + u) * (1/64)."""
+    q = np.asarray(keys_or_q).astype(np.uint64)
+    s, u = pl_x(b, inv_w, q)
+    u = np.minimum(u, np.float32(1.0)).astype(np.float32)
+    t = (s.astype(np.float32) + u).astype(np.float32)
+    return (t * np.float32(1.0 / MLP_STAGE1)).astype(np.float32)
 
 
 def max_error(leaf_hat: np.ndarray, leaf: np.ndarray) -> int:

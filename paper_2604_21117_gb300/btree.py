@@ -42,7 +42,8 @@ EXPORTED = ("bt_build", "bt_free", "bt_tree_info", "bt_tree_copy_image", "bt_sea
             "bt_check_timeouts", "bt_autotune", "bt_paper_node_bytes", "bt_paper_layout_build",
             "bt_paper_search_batch", "bt_paper_descend_sorted",
             "bt_server_create", "bt_server_submit", "bt_server_poll", "bt_server_drain", "bt_server_get_stats",
-            "bt_server_destroy", "bt_server_run_trace")
+            "bt_server_destroy", "bt_server_run_trace", "bt_range_build", "bt_range_free", "bt_range_info",
+            "bt_range_part", "bt_range_workspace_bytes", "bt_range_search")
 
 
 class bt_info(ctypes.Structure):
@@ -675,3 +676,58 @@ class BTree:
         bt_search_batch_host(self.handle, np.ascontiguousarray(h_queries), nq, vals, found, ws, nb, stream)
         (torch.cuda.current_stream() if stream is None else stream).synchronize()
         return vals, found
+
+
+# ------------------------------------------------------------ range partition
+
+_lib.bt_range_build.restype = _i
+_lib.bt_range_build.argtypes = [_vp, _vp, _u64, _i, _i, ctypes.c_uint32, ctypes.c_uint32, _vp, ctypes.POINTER(_vp)]
+_lib.bt_range_free.restype = None
+_lib.bt_range_free.argtypes = [_vp]
+_lib.bt_range_info.restype = _i
+_lib.bt_range_info.argtypes = [_vp, ctypes.POINTER(ctypes.c_uint32), _vp, _vp]
+_lib.bt_range_part.restype = _vp
+_lib.bt_range_part.argtypes = [_vp, ctypes.c_uint32]
+_lib.bt_range_workspace_bytes.restype = _u64
+_lib.bt_range_workspace_bytes.argtypes = [_vp, _u64]
+_lib.bt_range_search.restype = _i
+_lib.bt_range_search.argtypes = [_vp, _vp, _u64, _vp, _vp, _vp, _u64, _vp]
+
+
+def bt_range_build(h_keys: np.ndarray, h_vals: np.ndarray, fanout: int, parts: int, stream=None) -> int:
+    k = np.ascontiguousarray(h_keys)
+    v = np.ascontiguousarray(h_vals)
+    out = _vp()
+    st = _lib.bt_range_build(k.ctypes.data, v.ctypes.data, k.size, _width(k.dtype), _width(v.dtype), fanout, parts,
+                             _stream_handle(stream), ctypes.byref(out))
+    _check("bt_range_build", st)
+    return out.value
+
+
+def bt_range_free(r: int) -> None:
+    _lib.bt_range_free(r)
+
+
+def bt_range_info(r: int):
+    """(parts, splitters uint64[P-1], keys per part uint64[P])."""
+    p = ctypes.c_uint32()
+    _check("bt_range_info", _lib.bt_range_info(r, ctypes.byref(p), None, None))
+    sp = np.zeros(max(p.value - 1, 1), np.uint64)
+    nk = np.zeros(p.value, np.uint64)
+    _check("bt_range_info", _lib.bt_range_info(r, ctypes.byref(p), sp.ctypes.data, nk.ctypes.data))
+    return int(p.value), sp[: p.value - 1], nk
+
+
+def bt_range_part(r: int, p: int) -> int | None:
+    return _lib.bt_range_part(r, p)
+
+
+def bt_range_workspace_bytes(r: int, nq: int) -> int:
+    return int(_lib.bt_range_workspace_bytes(r, nq))
+
+
+def bt_range_search(r: int, d_queries, nq: int, d_out_vals, d_out_found, d_workspace, ws_bytes: int,
+                    stream=None) -> None:
+    st = _lib.bt_range_search(r, _dptr(d_queries), nq, _dptr(d_out_vals), _dptr(d_out_found), _dptr(d_workspace),
+                              ws_bytes, _stream_handle(stream))
+    _check("bt_range_search", st)

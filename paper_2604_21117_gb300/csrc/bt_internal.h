@@ -36,7 +36,8 @@ struct DevTree {
     int warps;           // warps per descent block
     int staging;         // BT_STAGE_*: pipelined (default), or synchronous with cp.async / bulk copies
     int lane_queries;    // queries per lane of the plain descent: 1 (32 per warp) or 2 (64 per warp)
-    int inner_stage;     // pipelined descent: inner levels read through L1 (0) or staged with cp.async (1)
+    int inner_stage;     // pipelined descent: inner levels through L1 (0), staged with cp.async (1), or
+                         // staged for partitioned batches and through L1 otherwise (2)
     int rank_ballot;     // pipelined descent: leaf rank by binary search (0) or warp ballot + popc (1)
     // Splitters of the batch partition: the largest keys of nsplit evenly
     // spaced leaves, and nsplit + 1 reciprocal widths of the key segments

@@ -182,7 +182,7 @@ extern "C" bt_status bt_tree_set_staging(bt_tree *t, uint32_t mode)
 
 extern "C" bt_status bt_tree_set_descent(bt_tree *t, uint32_t inner_staged, uint32_t rank_ballot)
 {
-    if (!t || inner_staged > 1 || rank_ballot > 1) return BT_ERR_ARG;
+    if (!t || inner_staged > 2 || rank_ballot > 1) return BT_ERR_ARG;
     t->dev.inner_stage = static_cast<int>(inner_staged);
     t->dev.rank_ballot = static_cast<int>(rank_ballot);
     return BT_OK;
@@ -338,7 +338,7 @@ extern "C" bt_status bt_build(const void *h_keys, const void *h_vals, uint64_t n
     d.warps = 8;
     d.lane_queries = 1;
     d.staging = BT_STAGE_PIPELINED;
-    d.inner_stage = 1;
+    d.inner_stage = 2;  // staged for partitioned batches, through L1 otherwise
     set_pin_levels(d, t->info, 16384);
 
     // Shape arithmetic: children (or keys, for leaves) per node.

@@ -149,7 +149,10 @@ __device__ __forceinline__ void leaf_rank_round(const K *stage, int rb, int nu, 
 #define BT_DESCEND_REGS __launch_bounds__(kDescWarpsMax * 32)
 #endif
 
-template <typename K, typename V, int M, bool COUNT, bool LEARN>
+// MODEL: kModelNone for the plain descent, kModelPL or kModelMLP for the
+// learned one (separate instantiations, so that the MLP's registers do not
+// limit the others).
+template <typename K, typename V, int M, bool COUNT, int MODEL>
 __global__ void BT_DESCEND_REGS k_descend(
     const DevTree t, const RawOf<K> *__restrict__ q, const uint32_t *__restrict__ qidx,
     const PartRec<K> *__restrict__ recs, uint64_t nq, V *__restrict__ out_v, uint8_t *__restrict__ out_f,
@@ -161,6 +164,7 @@ __global__ void BT_DESCEND_REGS k_descend(
     constexpr int CH = BLK / 16;  // 16-byte pieces per node block
     constexpr int SL = leaf_slots<K, M>();
     constexpr int SI = inner_slots<K, M>();
+    constexpr bool LEARN = MODEL != kModelNone;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const bool istage = !LEARN && t.inner_stage != 0;
     const bool ballot = t.rank_ballot != 0;
@@ -192,7 +196,7 @@ __global__ void BT_DESCEND_REGS k_descend(
     const float *minv = md.inv_w, *mslope = md.slope, *micpt = md.icpt, *mmlp = md.mlp;
     if constexpr (LEARN) {
         if (mbytes) {
-            if (md.kind == kModelPL) {
+            if constexpr (MODEL == kModelPL) {
                 const uint32_t S = md.segments;
                 uint64_t *sb = reinterpret_cast<uint64_t *>(msm);
                 float *sf = reinterpret_cast<float *>(msm + S * 8u);
@@ -272,7 +276,11 @@ __global__ void BT_DESCEND_REGS k_descend(
                 // windows (unsorted batches) are checked lane by lane in
                 // global memory.
                 const uint32_t L = md.leaves;
-                const uint32_t hat = model_leaf(md, mb, minv, mslope, micpt, mmlp, static_cast<uint64_t>(key));
+                uint32_t hat;
+                if constexpr (MODEL == kModelPL)
+                    hat = leaf_from_pred(pl_predict(mb, minv, mslope, micpt, md.segments, static_cast<uint64_t>(key)), L);
+                else
+                    hat = model_leaf(md, mb, minv, mslope, micpt, mmlp, static_cast<uint64_t>(key));
                 const uint32_t er = __ldg(md.errs + err_range(hat, L));
                 const uint32_t lo = hat > er ? hat - er : 0u;
                 const uint32_t hi = (static_cast<uint64_t>(hat) + er < L) ? hat + er : L - 1;
@@ -284,6 +292,17 @@ __global__ void BT_DESCEND_REGS k_descend(
                 if (staged) {
                     for (uint32_t j = lane; j <= whi - wlo; j += 32) lmstage[j] = lm[wlo + j];
                     __syncwarp();
+                }
+                if (!staged) {
+                    // this lane's window, read through L1: prefetch its lines
+                    // (up to four of 128 bytes), then search them
+                    const uint32_t first = lo > 0 ? lo - 1 : 0;
+                    const unsigned char *w0 = reinterpret_cast<const unsigned char *>(lm + first);
+                    const unsigned char *w1 = reinterpret_cast<const unsigned char *>(lm + hi) + sizeof(K);
+                    const uintptr_t l0 = reinterpret_cast<uintptr_t>(w0) & ~uintptr_t(127);
+                    if (reinterpret_cast<uintptr_t>(w1) - l0 <= 4 * 128)
+                        for (uintptr_t a = l0; a < reinterpret_cast<uintptr_t>(w1); a += 128)
+                            prefetch_l1(reinterpret_cast<const void *>(a));
                 }
                 auto leaf_max = [&](uint32_t j) -> K { return staged ? lmstage[j - wlo] : ld_key(lm + j); };
                 const bool low_ok = (lo == 0) || (leaf_max(lo - 1) < key);
@@ -454,18 +473,23 @@ static cudaError_t launch_with_window(void (*kern)(KArgs...), unsigned grid, int
     return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
-template <typename K, typename V, int M, bool COUNT, bool LEARN>
+template <typename K, typename V, int M, bool COUNT, int MODEL>
 static cudaError_t launch_pipe(const DescendArgs &a, cudaStream_t s)
 {
-    const DevTree &t = *a.t;
+    // inner levels staged (1) or through L1 (0); "auto" (2) stages them for a
+    // partitioned batch, whose warps meet one or two nodes per level, and not
+    // for an unsorted one, whose warps meet up to 32
+    constexpr bool LEARN = MODEL != kModelNone;
+    DevTree t = *a.t;
+    const bool istage = !LEARN && (t.inner_stage == 1 || (t.inner_stage == 2 && a.recs != nullptr));
+    t.inner_stage = istage ? 1 : 0;
     const int nw = t.warps > 0 ? t.warps : kDescWarpsDefault;
-    const bool istage = !LEARN && t.inner_stage != 0;
     ModelDev none;
     memset(&none, 0, sizeof(none));
     const ModelDev &md = a.md ? *a.md : none;
     const int mbytes = LEARN ? static_cast<int>(model_smem_bytes(md)) : 0;
     const int smem = static_cast<int>(t.pin_bytes) + mbytes + nw * pipe_smem_per_warp<K, M, LEARN>(istage);
-    auto kern = k_descend<K, V, M, COUNT, LEARN>;
+    auto kern = k_descend<K, V, M, COUNT, MODEL>;
     constexpr int max_model = LEARN ? static_cast<int>(kModelSmemSegments) * 20 : 0;
     cudaError_t e = ensure_dyn_smem(reinterpret_cast<const void *>(kern),
                                     kPinBudgetMax + max_model + kDescWarpsMax * pipe_smem_per_warp<K, M, LEARN>(true));
@@ -483,10 +507,13 @@ template <typename K, typename V, int M>
 static cudaError_t pipe_mode(const DescendArgs &a, cudaStream_t s)
 {
     if constexpr (!std::is_same<K, Key32>::value) {
-        if (a.md) return launch_pipe<K, V, M, false, true>(a, s);
+        if (a.md) {
+            if (a.md->kind == kModelPL) return launch_pipe<K, V, M, false, kModelPL>(a, s);
+            return launch_pipe<K, V, M, false, kModelMLP>(a, s);
+        }
     }
-    if (a.fetch) return launch_pipe<K, V, M, true, false>(a, s);
-    return launch_pipe<K, V, M, false, false>(a, s);
+    if (a.fetch) return launch_pipe<K, V, M, true, kModelNone>(a, s);
+    return launch_pipe<K, V, M, false, kModelNone>(a, s);
 }
 
 template <typename K, typename V>

@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(kMlpBlock) k_mlp_grad(const float *__restrict_
             const uint64_t r = splitmix64(seed ^ ((static_cast<uint64_t>(step) << 32) | i)) % n;
             uint64_t leaf;
             const uint64_t key = key_of_rank<K>(t, r, leaf);
-            x = mlp_x(key, md.kmin, md.kmax, md.inv_range);
+            x = mlp_x_rank(md.b, md.inv_w, key);
             tv = md.leaves > 1 ? __fdiv_rn(static_cast<float>(leaf), static_cast<float>(md.leaves - 1)) : 0.0f;
         } else {
             x = xs[i];
@@ -315,6 +315,8 @@ static bt_status train_impl(const bt_tree *tree, const bt_learn_opts *o, cudaStr
         k_pl_solve<<<(S + 255) / 256, 256, 0, s>>>(S, sums, const_cast<float *>(md.slope),
                                                    const_cast<float *>(md.icpt));
     } else {
+        // the first stage: breakpoints at key quantiles, as the PL model's
+        k_pl_breaks<K><<<1, 256, 0, s>>>(t, kMlpStage1, const_cast<uint64_t *>(md.b), const_cast<float *>(md.inv_w));
         float *p = const_cast<float *>(md.mlp);
         float *g = p + kMlpParams, *m1 = g + kMlpParams, *m2 = m1 + kMlpParams, *loss = m2 + kMlpParams;
         e = cudaMemcpyAsync(p, o->h_init, kMlpParams * sizeof(float), cudaMemcpyHostToDevice, s);
@@ -396,6 +398,10 @@ extern "C" bt_status bt_model_train(const bt_tree *tree, const bt_learn_opts *op
         off = a256(off + S * 4ull);
         off = a256(off + S * 5ull * 8ull + 256);  // fit sums (aligned after icpt)
     } else {
+        off_b = off;
+        off = a256(off + kMlpStage1 * 8ull);
+        off_inv = off;
+        off = a256(off + kMlpStage1 * 4ull);
         off_mlp = off;
         off = a256(off + (4ull * kMlpParams + 1) * 4ull);
     }
@@ -420,6 +426,8 @@ extern "C" bt_status bt_model_train(const bt_tree *tree, const bt_learn_opts *op
         md.slope = reinterpret_cast<const float *>(base + off_slope);
         md.icpt = reinterpret_cast<const float *>(base + off_icpt);
     } else {
+        md.b = reinterpret_cast<const uint64_t *>(base + off_b);
+        md.inv_w = reinterpret_cast<const float *>(base + off_inv);
         md.mlp = reinterpret_cast<const float *>(base + off_mlp);
     }
     m->info.kind = opts->kind;

@@ -15,8 +15,11 @@
 //       segment of q = largest s with b_s <= q (0 below b_0);
 //       x = fp32(fp64(q - b_s)) * inv_w_s,  inv_w_s = fp32(1 / fp64(b_{s+1} - b_s));
 //       pred = fp32(fp32(slope_s * x) + icpt_s), separately rounded.
-//   MLP (1 -> 32 -> 32 -> 1, ReLU): x = fp32(fp64(clamp(q) - kmin)) * inv_range;
-//       pred = (w3 . relu(W2 relu(W1 x + b1) + b2) + b3) * (L - 1).
+//   MLP (1 -> 32 -> 32 -> 1, ReLU) on a rank coordinate (a two-stage model):
+//       the first stage is kMlpStage1 breakpoints b_s at key quantiles, as the
+//       PL model's; x = fp32(fp32(s) + min(fp32(fp64(q - b_s)) * inv_w_s, 1))
+//       * (1 / kMlpStage1), so that x follows the key's rank whatever the key
+//       distribution; pred = (w3 . relu(W2 relu(W1 x + b1) + b2) + b3) * (L - 1).
 //   leaf_hat = rint(clamp(pred, 0, L - 1)).
 #pragma once
 
@@ -27,6 +30,7 @@
 namespace btgb {
 
 constexpr int kMlpH = 32;
+constexpr uint32_t kMlpStage1 = 64;  // breakpoints of the MLP's first stage
 constexpr int kMlpParams = kMlpH + kMlpH + kMlpH * kMlpH + kMlpH + kMlpH + 1;  // 1153
 // parameter offsets: W1[32], b1[32], W2[32][32] (row = output unit), b2[32], w3[32], b3
 constexpr int kOffW1 = 0, kOffB1 = 32, kOffW2 = 64, kOffB2 = 64 + 1024, kOffW3 = 64 + 1024 + 32,
@@ -84,6 +88,16 @@ __device__ __forceinline__ float pl_predict(const uint64_t *b, const float *inv_
     return __fadd_rn(__fmul_rn(slope[s], x), icpt[s]);
 }
 
+// The MLP's input: the rank coordinate of q from the first stage's
+// breakpoints (b, inv_w: kMlpStage1 entries, any address space).
+__device__ __forceinline__ float mlp_x_rank(const uint64_t *b, const float *inv_w, uint64_t q)
+{
+    const int s = pl_segment(b, kMlpStage1, q);
+    const uint64_t diff = q >= b[s] ? q - b[s] : 0ull;
+    const float u = fminf(__fmul_rn(__double2float_rn(__ull2double_rn(diff)), inv_w[s]), 1.0f);
+    return __fmul_rn(__fadd_rn(static_cast<float>(s), u), 1.0f / static_cast<float>(kMlpStage1));
+}
+
 __device__ __forceinline__ float mlp_x(uint64_t q, uint64_t kmin, uint64_t kmax, float inv_range)
 {
     const uint64_t c = q < kmin ? kmin : (q > kmax ? kmax : q);
@@ -120,7 +134,7 @@ __device__ __forceinline__ uint32_t model_leaf(const ModelDev &m, const uint64_t
                                                uint64_t q)
 {
     if (m.kind == kModelPL) return leaf_from_pred(pl_predict(b, inv_w, slope, icpt, m.segments, q), m.leaves);
-    const float y = mlp_forward(mlp, mlp_x(q, m.kmin, m.kmax, m.inv_range));
+    const float y = mlp_forward(mlp, mlp_x_rank(b, inv_w, q));
     return leaf_from_pred(__fmul_rn(y, static_cast<float>(m.leaves - 1)), m.leaves);
 }
 

@@ -148,3 +148,16 @@ def test_paper_layout_entry_points_check_arguments(bt):
     assert e.value.code == "BT_ERR_ARG"
     bt.bt_paper_search_batch(h, 0, 0, 0, 0, 0, 0, stream=0)  # nq = 0 is a no-op
     bt.bt_free(h)
+
+
+def test_range_build_rejects_bad_arguments_before_touching_the_gpu(bt):
+    import ctypes
+    lib = bt._lib
+    keys = np.arange(10, dtype=np.uint64)
+    out = ctypes.c_void_p()
+    for parts in (0, 65, 11):  # none, too many, more than keys
+        assert lib.bt_range_build(keys.ctypes.data, keys.ctypes.data, 10, 8, 8, 16, parts, None,
+                                  ctypes.byref(out)) == 1
+    assert lib.bt_range_build(keys.ctypes.data, keys.ctypes.data, 10, 32, 8, 16, 2, None, ctypes.byref(out)) == 1
+    assert lib.bt_range_workspace_bytes(None, 100) == 0
+    assert lib.bt_range_part(None, 0) is None

@@ -149,3 +149,53 @@ def pins_lookup(keys, vals, q):
     v = np.full(q.size, np.uint64(2**64 - 1))
     v[hit] = vals[pos[hit]]
     return v, hit.astype(np.uint8)
+
+
+def _range_rank_main(rank, world, port, out):
+    """Rank r holds part r of the key set (a CPU oracle over its key range);
+    each rank routes its own batch to the parts' ranks and gets its results
+    back in input order."""
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    import torch.distributed as dist
+    from paper_2604_21117_gb300 import range_split as RS
+    bench.dist_init(world, "gloo")
+    keys = W.uniform_keys(40_000, 64, seed=95)
+    vals = W.rank_values(keys.size, 64)
+    lo, hi = RS.part_bounds(keys.size, world, rank)
+    part = OracleTree(keys[lo:hi], vals[lo:hi], 16)
+    split = RS.splitters(keys, world)
+    # every query lands in one part; misses below the first and above the last key too
+    q = W.make_queries(keys, 3000 + 777 * rank, 0.7, seed=96 + rank, width_bits=64, zipf_s=1.1)
+    q[:3] = [0, 2**64 - 1, keys[lo]]
+    v, f = RS.exchange_search(q, split, lambda k: part.search(k)[:2], world)
+    part.close()
+    out[rank] = (q.tobytes(), v.tobytes(), f.tobytes())
+    dist.destroy_process_group()
+
+
+def test_range_split_exchange_over_two_gloo_ranks():
+    import torch.multiprocessing as mp
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_range_rank_main, args=(2, _free_port(), out), nprocs=2, start_method="spawn")
+    keys = W.uniform_keys(40_000, 64, seed=95)
+    vals = W.rank_values(keys.size, 64)
+    for r in range(2):
+        q = np.frombuffer(out[r][0], np.uint64)
+        ev, ef = pins_lookup(keys, vals, q)
+        assert np.array_equal(np.frombuffer(out[r][1], np.uint64), ev)
+        assert np.array_equal(np.frombuffer(out[r][2], np.uint8), ef)
+
+
+def test_range_split_routes_by_part_ranges():
+    from paper_2604_21117_gb300 import range_split as RS
+    keys = W.uniform_keys(1000, 64, seed=97)
+    for parts in (1, 2, 3, 7):
+        split = RS.splitters(keys, parts)
+        assert split.size == parts - 1
+        dest = RS.route(keys, split)
+        for p in range(parts):
+            lo, hi = RS.part_bounds(keys.size, parts, p)
+            assert np.all(dest[lo:hi] == p)  # every stored key routes to the part that holds it
+        assert RS.route(np.array([0, 2**64 - 1], np.uint64), split).tolist() == [0, parts - 1]

@@ -73,7 +73,7 @@ def test_mlp_training_lowers_the_loss(bt):
     p0 = W.mlp_init_params(45)
     _, _, leaf, _ = OracleTree(keys, keys, 32).search(keys)
     L = tree.level_nodes[-1]
-    x = LO.mlp_x(keys, int(keys[0]), int(keys[-1]))
+    x = LO.mlp_x(keys, *LO.mlp_stage1(keys))
     loss0 = LO.mlp_loss(p0, x, leaf / (L - 1))
     mdl = bt.bt_model_train(tree.handle, bt.BT_MODEL_MLP, h_init=p0, steps=300, batch=4096, lr=3e-3, seed=46)
     p1 = bt.bt_model_copy_params(mdl)
@@ -82,6 +82,24 @@ def test_mlp_training_lowers_the_loss(bt):
     info = bt.bt_model_get_info(mdl)
     assert info.max_err < L and np.isfinite(info.final_loss)
     bt.bt_model_free(mdl)
+
+
+def test_mlp_rank_input_bounds_lognormal_keys(bt):
+    """On keys from the lognormal mixture the MLP, fed the first stage's rank
+    coordinate, learns the leaf to a small fraction of the leaves (an input
+    scaled over the key range could not: the CDF rises within the first
+    millionth of that range)."""
+    keys = W.lognormal_mixture_keys(1 << 20, seed=49)
+    tree = bt.BTree(keys, W.rank_values(keys.size, 64), 32)
+    L = tree.level_nodes[-1]
+    mdl = bt.bt_model_train(tree.handle, bt.BT_MODEL_MLP, h_init=W.mlp_init_params(50), steps=1000, batch=16384,
+                            lr=2e-3, seed=51)
+    info = bt.bt_model_get_info(mdl)
+    assert info.max_err < L // 8, (info.max_err, L)
+    o = OracleTree(keys, W.rank_values(keys.size, 64), 32)
+    _learned_check(bt, tree, o, mdl, W.make_queries(keys, 50_000, 0.9, seed=52, width_bits=64))
+    bt.bt_model_free(mdl)
+    tree.close()
 
 
 def _learned_check(bt, tree, o, mdl, q, stats=None):

@@ -96,10 +96,22 @@ def test_mlp_gradient_matches_central_differences():
     assert np.allclose(ana, num, rtol=1e-5, atol=1e-8)
 
 
-def test_mlp_x_normalisation():
-    x = LO.mlp_x(np.array([5, 5, 10, 15, 99], np.uint64), 5, 15)
-    assert x.dtype == np.float32
-    assert list(x) == [0.0, 0.0, np.float32(0.5), np.float32(1.0), np.float32(1.0)]
+def test_mlp_x_rank_coordinate():
+    """The first stage maps a key to its rank fraction: exactly s/64 at the
+    s-th breakpoint, 0 below the smallest key, at most 1, non-decreasing in
+    the key, and within one segment (1/64) of rank/n whatever the key
+    distribution."""
+    for keys in (W.uniform_keys(10_000, 64, seed=11), W.lognormal_mixture_keys(10_000, seed=12)):
+        b, inv_w = LO.mlp_stage1(keys)
+        assert b.size == 64 and np.array_equal(b, keys[(np.arange(64) * keys.size) // 64])
+        xb = LO.mlp_x(b, b, inv_w)
+        assert xb.dtype == np.float32 and np.array_equal(xb, (np.arange(64) / 64).astype(np.float32))
+        x = LO.mlp_x(keys, b, inv_w)
+        assert np.all(np.diff(x.astype(np.float64)) >= 0)
+        assert x.min() >= 0 and x.max() <= 1
+        rank = np.arange(keys.size) / keys.size
+        assert np.max(np.abs(x - rank)) <= 1 / 64 + 1e-6
+        assert LO.mlp_x(np.array([0], np.uint64), b, inv_w)[0] == 0.0 or keys[0] == 0
 
 
 def test_range_errors_brute_force():
