@@ -341,26 +341,63 @@ typedef struct bt_batch_desc {
 
 typedef struct bt_forest bt_forest;
 
-/* A device table of `count` built trees with equal key and value widths
- * (fanouts may differ; integer keys only: BT_ERR_ARG for 32-byte keys).
- * The trees must outlive the forest. */
+/* A table of `count` built trees with equal key and value widths (fanouts
+ * may differ; integer keys only: BT_ERR_ARG for 32-byte keys).  Each tree
+ * brings its own launch settings as bt_autotune (or bt_tree_set_launch,
+ * bt_tree_set_staging, bt_tree_set_lane_queries, bt_tree_set_descent) left
+ * them: its pinned top levels (trimmed, deepest level of the tree pinning
+ * most first, until all trees' pinned levels fit the forest's shared-memory
+ * budget), its queries per lane, and whether the levels below the pinned
+ * ones are staged per warp (the synchronous designs and inner-staged
+ * pipelined design) or read lane by lane through L1 (the pipelined design).
+ * Warps per block default to the setting of the tree with the most keys,
+ * the pin budget to 32 KB.  The trees must outlive the forest.
+ * Errors: BT_ERR_ARG, BT_ERR_NOMEM, BT_ERR_CUDA. */
 bt_status bt_forest_create(const bt_tree *const *trees, uint32_t count, bt_forest **out);
+
+/* The same with a learned leaf predictor per tree: models[i] NULL (plain
+ * descent) or a model trained on trees[i] (BT_ERR_ARG otherwise, or for a
+ * model on an empty tree).  A query whose model window proves its leaf
+ * skips the inner levels, the others walk them (bt_learned_search_batch's
+ * rule, applied lane by lane); trees with a model are read through L1.
+ * Models must outlive the forest. */
+bt_status bt_forest_create_learned(const bt_tree *const *trees, const bt_model *const *models, uint32_t count,
+                                   bt_forest **out);
 void bt_forest_free(bt_forest *forest);
+
+/* Launch settings of a forest. */
+typedef struct bt_forest_tune {
+    uint32_t warps_per_block; /* 1..16 */
+    uint32_t pin_budget;      /* shared-memory bytes for all trees' pinned levels, 0..98304 */
+    uint32_t lane_queries;    /* 0: each tree's own, 1 or 2: that many queries per lane for all trees */
+    uint32_t staging;         /* 0: each tree's own design, 1: all read through L1, 2: all staged per warp */
+    uint32_t pin_applied;     /* out: bytes of pinned levels the budget admitted */
+    float us;                 /* out (bt_forest_autotune): median time of the work list */
+} bt_forest_tune;
+
+/* Replace a forest's launch settings (synchronizes the device; CUDA graphs
+ * captured before keep the old shape and must be captured again).
+ * Errors: BT_ERR_ARG (null or out-of-range values), BT_ERR_CUDA. */
+bt_status bt_forest_set_launch(bt_forest *forest, const bt_forest_tune *settings);
+bt_status bt_forest_get_launch(const bt_forest *forest, bt_forest_tune *out);
 
 /* Device workspace for a work list of nbatches batches. */
 uint64_t bt_forest_workspace_bytes(uint32_t nbatches);
 
 /*
  * bt_forest_search -- every batch of the device work list d_batches[0..n) in
- * one persistent launch: 32-query chunks of all batches are shared out over
- * resident warps; each chunk descends its tree level by level (each distinct
- * node of the chunk staged once per level, Sec. IV-A) and writes value and
- * found flag at its queries' positions.  Batches are not sorted (they are
- * small; the per-warp distinct-node staging already reuses nodes).
+ * one persistent launch: the batches' chunks (32 queries, or 64 for a tree
+ * at two queries per lane) are shared out over resident warps; each chunk
+ * descends its tree level by level (Sec. IV-A) -- pinned levels from the
+ * block's shared copy, the others staged per warp (each distinct node of the
+ * chunk loaded once) or read through L1 (lanes sharing a node share its
+ * lines) -- and writes value and found flag at its queries' positions.
+ * Batches are not sorted (they are small, and unsorted chunks meet many
+ * nodes per level).
  *   d_queries        nq keys (device); results go to the same positions of
  *                    d_out_vals / d_out_found (nq entries each).
  *   nq               length of those three arrays.
- *   warps_per_block  1..16, 0 = 8 (a tuning knob, see bt_autotune).
+ *   warps_per_block  1..16, 0 = the forest's setting.
  * Each work-list entry must name a tree below the forest's count and lie
  * inside the arrays (offset + count <= nq).  The kernel checks both: an
  * entry that breaks either is skipped (nothing is written for it) and
@@ -371,6 +408,20 @@ uint64_t bt_forest_workspace_bytes(uint32_t nbatches);
 bt_status bt_forest_search(const bt_forest *forest, const bt_batch_desc *d_batches, uint32_t nbatches,
                            const void *d_queries, uint64_t nq, void *d_out_vals, uint8_t *d_out_found,
                            void *d_workspace, uint64_t ws_bytes, uint32_t warps_per_block, bt_stream stream);
+
+/*
+ * bt_forest_autotune -- time the work list (arguments as bt_forest_search)
+ * under every combination of warps per block {4, 8, 16}, pin budget
+ * {0, 16384, 49152, 98304}, queries per lane {each tree's, 1, 2} and
+ * staging {each tree's, all through L1, all staged}; keep the fastest (median
+ * of 5 timed runs after 2 untimed, CUDA events on `stream`) as the forest's
+ * settings and return it in *best.  Synchronizes the device.  No counterpart
+ * in the paper (its kernel's shape is fixed by the FPGA build).
+ * Errors: as bt_forest_search.
+ */
+bt_status bt_forest_autotune(bt_forest *forest, const bt_batch_desc *d_batches, uint32_t nbatches,
+                             const void *d_queries, uint64_t nq, void *d_out_vals, uint8_t *d_out_found,
+                             void *d_workspace, uint64_t ws_bytes, bt_stream stream, bt_forest_tune *best);
 
 /* Work-list entries that bt_forest_search skipped since the last call (a
  * tree index outside the forest, or queries beyond the arrays), read and
@@ -567,15 +618,23 @@ bt_status bt_paper_descend_sorted(const bt_tree *tree, const void *d_queries, co
  * host that writes a batch, runs the kernel and reads the results, and
  * notes that a pipelined host overlaps its transfers with the kernel
  * (Sec. V-B, Fig. 7).  A server keeps trees resident and serves requests
- * from many callers: a worker thread coalesces waiting requests of one tree
- * into a batch when the oldest has waited deadline_us or the batch is full,
- * and runs it on a free slot (own stream, page-locked staging, device
- * buffers, workspace): copy in, search, copy out.  Up to `slots` batches are
- * in flight at once, so their work overlaps on the device while new requests
- * are admitted into later batches as slots free up.  A batch is issued only
- * while the staging bytes of all batches in flight stay within
- * mem_cap_bytes; submissions beyond pending_cap_bytes of waiting requests
- * are refused with BT_ERR_NOMEM (back-pressure).
+ * from many callers.  A submission copies the request's keys into its
+ * tree's ring of lookups in page-locked, device-mapped host memory.  A
+ * worker thread forms a batch when the oldest waiting request has waited
+ * deadline_us or max_batch lookups are waiting: it takes waiting requests of
+ * every tree (oldest tree first) and runs them as one multi-tree launch
+ * (bt_forest_search's kernel, each tree with its own launch settings and
+ * model) on a free slot (its own stream); the kernel reads the keys from the
+ * rings, writes the results back into them and raises the slot's flag in
+ * host memory -- one API call per batch, no copies.  Up to `slots` batches
+ * are in flight at once, so their work overlaps on the device while new
+ * requests are admitted into later batches as slots free up; batches retire
+ * in issue order, their results copied into the requests' buffers.  A
+ * batch is issued only while the bytes (keys, values, flags) of all batches
+ * in flight stay within mem_cap_bytes; submissions beyond pending_cap_bytes
+ * of waiting requests, or beyond a tree's ring (max_batch * (slots + 2)
+ * lookups, at least 2 * max_batch, at most 2^22 unless 2 * max_batch is
+ * more), are refused with BT_ERR_NOMEM (back-pressure).
  * ------------------------------------------------------------------------ */
 typedef struct bt_server bt_server;
 
@@ -583,7 +642,7 @@ typedef struct bt_server_opts {
     uint32_t slots;             /* batches in flight at once, 1..64 */
     uint32_t max_batch;         /* queries per batch, 1..2^24 (also the largest request) */
     double deadline_us;         /* longest a request waits to be batched */
-    uint64_t mem_cap_bytes;     /* staging bytes of batches in flight (0 = unlimited) */
+    uint64_t mem_cap_bytes;     /* bytes (keys, values, flags) of batches in flight (0 = unlimited) */
     uint64_t pending_cap_bytes; /* bytes of waiting requests before refusal (0 = unlimited) */
 } bt_server_opts;
 
@@ -593,21 +652,22 @@ typedef struct bt_server_stats {
     float p50_us, p99_us, max_us; /* request latency, submission to results in place */
 } bt_server_stats;
 
-/* Start a server over `ntrees` resident trees (equal key and value widths).
- * models: NULL, or one entry per tree, NULL or a model trained on that tree
- * (its searches then use bt_learned_search_batch; a model for an empty tree
- * is BT_ERR_ARG).  Trees and models must
- * outlive the server.  Allocates the slots' buffers and starts the worker on
- * the current device.  Errors: BT_ERR_ARG, BT_ERR_NOMEM, BT_ERR_CUDA. */
+/* Start a server over `ntrees` resident trees (equal integer key and value
+ * widths; BT_ERR_ARG for 32-byte keys).  models: NULL, or one entry per
+ * tree, NULL or a model trained on that tree (its lookups then take the
+ * learned path of bt_forest_create_learned; a model for an empty tree is
+ * BT_ERR_ARG).  Trees and models must outlive the server.  Allocates the
+ * rings and slots and starts the worker on the current device.
+ * Errors: BT_ERR_ARG, BT_ERR_NOMEM, BT_ERR_CUDA. */
 bt_status bt_server_create(const bt_tree *const *trees, const bt_model *const *models, uint32_t ntrees,
                            const bt_server_opts *opts, bt_server **out);
 
-/* Queue one request of `count` keys (host memory, read when its batch is
- * formed) for tree number `tree`; the results are written to h_out_vals /
+/* Queue one request of `count` keys (host memory, copied before the call
+ * returns) for tree number `tree`; the results are written to h_out_vals /
  * h_out_found (host) before the request's ticket is reported done.  Buffers
  * must stay valid until then.  Thread-safe.  BT_ERR_NOMEM: the pending cap
- * is full now (retry later); BT_ERR_ARG: count is 0 or above max_batch, or
- * the request alone exceeds pending_cap_bytes.  If a batch cannot be issued
+ * or the tree's ring is full now (retry later); BT_ERR_ARG: count is 0 or
+ * above max_batch, or the request alone exceeds pending_cap_bytes.  If a batch cannot be issued
  * (a failing CUDA call), its requests are never reported done and every
  * later call returns the error. */
 bt_status bt_server_submit(bt_server *server, uint32_t tree, const void *h_keys, uint32_t count,

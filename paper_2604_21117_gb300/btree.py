@@ -36,8 +36,8 @@ EXPORTED = ("bt_build", "bt_free", "bt_tree_info", "bt_tree_copy_image", "bt_sea
             "bt_search_batch_host", "bt_search_batch_noalloc", "bt_status_str", "bt_last_error_detail",
             "bt_model_train", "bt_model_free", "bt_model_get_info", "bt_model_copy_params", "bt_mlp_grad",
             "bt_learned_descend_sorted", "bt_learned_search_batch", "bt_model_copy_err_bounds",
-            "bt_forest_create", "bt_forest_free",
-            "bt_forest_workspace_bytes", "bt_forest_search", "bt_forest_bad_batches", "bt_tree_set_launch", "bt_tree_set_staging",
+            "bt_forest_create", "bt_forest_create_learned", "bt_forest_free", "bt_forest_set_launch",
+            "bt_forest_get_launch", "bt_forest_autotune", "bt_forest_workspace_bytes", "bt_forest_search", "bt_forest_bad_batches", "bt_tree_set_launch", "bt_tree_set_staging",
             "bt_tree_set_lane_queries", "bt_tree_set_descent", "bt_tree_set_l2_window", "bt_debug_set_wait_polls",
             "bt_check_timeouts", "bt_autotune", "bt_paper_node_bytes", "bt_paper_layout_build",
             "bt_paper_search_batch", "bt_paper_descend_sorted",
@@ -358,12 +358,28 @@ class bt_tune(ctypes.Structure):
                 ("inner_staged", ctypes.c_uint32), ("us_per_batch", ctypes.c_float)]
 
 
+class bt_forest_tune(ctypes.Structure):
+    _fields_ = [("warps_per_block", ctypes.c_uint32), ("pin_budget", ctypes.c_uint32),
+                ("lane_queries", ctypes.c_uint32), ("staging", ctypes.c_uint32), ("pin_applied", ctypes.c_uint32),
+                ("us", ctypes.c_float)]
+
+
 BATCH_DESC_DTYPE = np.dtype([("tree", np.uint32), ("count", np.uint32), ("offset", np.uint64)])
 
 _lib.bt_forest_create.restype = _i
 _lib.bt_forest_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_uint32, ctypes.POINTER(_vp)]
+_lib.bt_forest_create_learned.restype = _i
+_lib.bt_forest_create_learned.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_uint32,
+                                          ctypes.POINTER(_vp)]
 _lib.bt_forest_free.restype = None
 _lib.bt_forest_free.argtypes = [_vp]
+_lib.bt_forest_set_launch.restype = _i
+_lib.bt_forest_set_launch.argtypes = [_vp, ctypes.POINTER(bt_forest_tune)]
+_lib.bt_forest_get_launch.restype = _i
+_lib.bt_forest_get_launch.argtypes = [_vp, ctypes.POINTER(bt_forest_tune)]
+_lib.bt_forest_autotune.restype = _i
+_lib.bt_forest_autotune.argtypes = [_vp, _vp, ctypes.c_uint32, _vp, _u64, _vp, _vp, _vp, _u64, _vp,
+                                    ctypes.POINTER(bt_forest_tune)]
 _lib.bt_forest_workspace_bytes.restype = _u64
 _lib.bt_forest_workspace_bytes.argtypes = [ctypes.c_uint32]
 _lib.bt_forest_search.restype = _i
@@ -395,8 +411,44 @@ def bt_forest_create(trees) -> int:
     return out.value
 
 
+def bt_forest_create_learned(trees, models) -> int:
+    """models: one entry per tree, a model handle or None (plain descent)."""
+    if len(models) != len(trees):
+        raise ValueError("one model entry per tree")
+    arr = (_vp * len(trees))(*[t if isinstance(t, int) else t.handle for t in trees])
+    marr = (_vp * len(models))(*[m if m else None for m in models])
+    out = _vp()
+    _check("bt_forest_create_learned", _lib.bt_forest_create_learned(arr, marr, len(trees), ctypes.byref(out)))
+    return out.value
+
+
 def bt_forest_free(forest: int) -> None:
     _lib.bt_forest_free(forest)
+
+
+def bt_forest_set_launch(forest: int, warps_per_block: int = 8, pin_budget: int = 32768, lane_queries: int = 0,
+                         staging: int = 0) -> None:
+    cfg = bt_forest_tune(warps_per_block, pin_budget, lane_queries, staging, 0, 0.0)
+    _check("bt_forest_set_launch", _lib.bt_forest_set_launch(forest, ctypes.byref(cfg)))
+
+
+def bt_forest_get_launch(forest: int) -> bt_forest_tune:
+    out = bt_forest_tune()
+    _check("bt_forest_get_launch", _lib.bt_forest_get_launch(forest, ctypes.byref(out)))
+    return out
+
+
+def bt_forest_autotune(forest: int, d_batches, nbatches: int, d_queries, d_out_vals, d_out_found, d_workspace,
+                       ws_bytes: int, stream=None, nq: int | None = None) -> bt_forest_tune:
+    """Time the work list under every forest launch setting; keeps and returns the fastest."""
+    if nq is None:
+        nq = int(d_queries.numel())
+    out = bt_forest_tune()
+    st = _lib.bt_forest_autotune(forest, _dptr(d_batches), nbatches, _dptr(d_queries), nq, _dptr(d_out_vals),
+                                 _dptr(d_out_found), _dptr(d_workspace), ws_bytes, _stream_handle(stream),
+                                 ctypes.byref(out))
+    _check("bt_forest_autotune", st)
+    return out
 
 
 def bt_forest_workspace_bytes(nbatches: int) -> int:

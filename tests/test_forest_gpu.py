@@ -174,3 +174,110 @@ def test_two_queries_per_lane(bt, m, kw, vw, nq):
     for sb in (-1, 0, 6):
         v, f = tree.search(torch.from_numpy(q).cuda(), sort_bits=sb)
         assert np.array_equal(v.cpu().numpy().astype(np.uint64), ov) and np.array_equal(f.cpu().numpy(), of), sb
+
+
+def _forest_outputs(bt, forest, desc, allq, d_desc, warps=0):
+    import torch
+    nb = desc.size
+    v = torch.zeros(max(1, allq.size), dtype=torch.uint64, device="cuda")
+    f = torch.full((max(1, allq.size),), 9, dtype=torch.uint8, device="cuda")
+    wsb = bt.bt_forest_workspace_bytes(nb)
+    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    bt.bt_forest_search(forest, d_desc, nb, torch.from_numpy(allq).cuda(), v, f, ws, wsb, warps, nq=allq.size)
+    return v, f
+
+
+@pytest.mark.parametrize("warps,pin,lq,staging", [(8, 32768, 0, 0), (4, 0, 1, 1), (16, 98304, 2, 1), (8, 16384, 1, 2),
+                                                  (4, 98304, 2, 2), (12, 49152, 0, 2), (1, 0, 2, 0)])
+def test_forest_settings_do_not_change_results(bt, warps, pin, lq, staging):
+    """Each tree keeps its own tuned design (two queries per lane, staged
+    levels, pinned levels) unless the forest overrides it; every combination
+    gives the oracle's results."""
+    trees, oracles, desc, qs, allq, d_desc = _forest_case(
+        bt, [3000, 150_000, 400_000, 1, 0], [16, 32, 64, 8, 32], 400, seed=91)
+    bt.bt_tree_set_lane_queries(trees[0].handle, 2)
+    bt.bt_tree_set_staging(trees[1].handle, bt.BT_STAGE_CP_ASYNC)
+    bt.bt_tree_set_launch(trees[2].handle, 8, 49152)
+    bt.bt_tree_set_launch(trees[0].handle, 8, 16384)
+    forest = bt.bt_forest_create(trees)
+    bt.bt_forest_set_launch(forest, warps, pin, lq, staging)
+    got = bt.bt_forest_get_launch(forest)
+    assert (got.warps_per_block, got.pin_budget, got.lane_queries, got.staging) == (warps, pin, lq, staging)
+    assert got.pin_applied <= pin
+    v, f = _forest_outputs(bt, forest, desc, allq, d_desc)
+    _check_forest(bt, oracles, desc, qs, v, f)
+    assert bt.bt_forest_bad_batches() == 0
+    bt.bt_forest_free(forest)
+
+
+def test_forest_pins_tuned_levels_within_its_budget(bt):
+    trees, oracles, desc, qs, allq, d_desc = _forest_case(bt, [300_000, 300_000, 300_000], [8, 16, 32], 60, seed=92)
+    for t in trees:
+        bt.bt_tree_set_launch(t.handle, 8, 49152)
+    forest = bt.bt_forest_create(trees)
+    for budget in (98304, 49152, 16384, 0):
+        bt.bt_forest_set_launch(forest, 8, budget, 0, 0)
+        got = bt.bt_forest_get_launch(forest)
+        assert got.pin_applied <= budget
+        if budget == 98304:
+            assert got.pin_applied > 16384  # the three trees' tuned pins, trimmed to fit
+        v, f = _forest_outputs(bt, forest, desc, allq, d_desc)
+        _check_forest(bt, oracles, desc, qs, v, f)
+    bt.bt_forest_free(forest)
+
+
+@pytest.mark.parametrize("lq", [0, 2])
+def test_learned_forest_matches_oracles(bt, lq):
+    """Trees with a PL model, an MLP model and none in one forest: lanes whose
+    window proves their leaf skip the inner levels, the others walk them."""
+    import torch  # noqa: F401
+    trees, oracles, desc, qs, allq, d_desc = _forest_case(bt, [50_000, 400_000, 2000], [32, 16, 8], 300, seed=93)
+    models = [bt.bt_model_train(trees[0].handle, bt.BT_MODEL_PL, segments=64),
+              bt.bt_model_train(trees[1].handle, bt.BT_MODEL_MLP, h_init=W.mlp_init_params(W.SEED_BASE + 5),
+                                steps=200, batch=4096, lr=2e-3, seed=94),
+              None]
+    forest = bt.bt_forest_create_learned(trees, models)
+    bt.bt_forest_set_launch(forest, 8, 16384, lq, 2)  # staging is ignored for trees with a model
+    v, f = _forest_outputs(bt, forest, desc, allq, d_desc)
+    _check_forest(bt, oracles, desc, qs, v, f)
+    bt.bt_forest_free(forest)
+    # a forest of PL models only
+    pl = [bt.bt_model_train(trees[i].handle, bt.BT_MODEL_PL, segments=256) for i in range(3)]
+    forest = bt.bt_forest_create_learned(trees, pl)
+    v, f = _forest_outputs(bt, forest, desc, allq, d_desc)
+    _check_forest(bt, oracles, desc, qs, v, f)
+    bt.bt_forest_free(forest)
+    for m in models[:2] + pl:
+        bt.bt_model_free(m)
+
+
+def test_learned_forest_rejects_a_model_of_another_tree(bt):
+    trees, _, _, _, _, _ = _forest_case(bt, [50_000, 400_000], [32, 16], 4, seed=95)
+    m = bt.bt_model_train(trees[0].handle, bt.BT_MODEL_PL, segments=64)
+    with pytest.raises(bt.BTreeError) as e:
+        bt.bt_forest_create_learned(trees, [None, m])
+    assert e.value.code == "BT_ERR_ARG"
+    bt.bt_model_free(m)
+
+
+def test_forest_autotune_keeps_the_fastest_correct_settings(bt):
+    import torch
+    trees, oracles, desc, qs, allq, d_desc = _forest_case(bt, [1000, 100_000, 500_000], [8, 32, 16], 800, seed=96)
+    forest = bt.bt_forest_create(trees)
+    nb = desc.size
+    dq = torch.from_numpy(allq).cuda()
+    v = torch.empty(allq.size, dtype=torch.uint64, device="cuda")
+    f = torch.empty(allq.size, dtype=torch.uint8, device="cuda")
+    wsb = bt.bt_forest_workspace_bytes(nb)
+    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    best = bt.bt_forest_autotune(forest, d_desc, nb, dq, v, f, ws, wsb)
+    assert best.warps_per_block in (4, 8, 16) and best.pin_budget in (0, 16384, 49152, 98304)
+    assert best.lane_queries in (0, 1, 2) and best.staging in (0, 1, 2) and best.us > 0
+    got = bt.bt_forest_get_launch(forest)
+    assert (got.warps_per_block, got.pin_budget, got.lane_queries, got.staging) == \
+        (best.warps_per_block, best.pin_budget, best.lane_queries, best.staging)
+    v.zero_()
+    f.fill_(9)
+    bt.bt_forest_search(forest, d_desc, nb, dq, v, f, ws, wsb)
+    _check_forest(bt, oracles, desc, qs, v, f)
+    bt.bt_forest_free(forest)

@@ -5,7 +5,8 @@ against a CPU search, Sec. V-A):
 - batching: one CUDA-graph replay of a persistent launch over 10,000 batches
   (sizes log-uniform in 1..1024, Zipf(0.9) queries, 80% hits) addressed to
   four trees of 10^3, 10^5, 10^6 and 2*10^7 uint64 keys whose fanouts and
-  launch settings the autotuner chose;
+  launch settings the autotuner chose, with the forest's launch shape from
+  the forest autotuner (tuned on the first 1000 batches);
 - learned: 2^24 uint64 keys from the three-lognormal mixture, fanout 32, the
   256-segment piecewise-linear model and the 1-32-32-1 MLP, batches of 1024
   and 2^20 at 90% hits;
@@ -76,13 +77,15 @@ def test_batching_config_full_size(bt):
     f = torch.full((off,), 9, dtype=torch.uint8, device="cuda")
     wsb = bt.bt_forest_workspace_bytes(nbatches)
     ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    # the forest's launch shape chosen by its autotuner, as the benchmark does
+    bt.bt_forest_autotune(forest, d_desc[: 16 * 1000], 1000, dq, v, f, ws, wsb)
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
-        bt.bt_forest_search(forest, d_desc, nbatches, dq, v, f, ws, wsb, 8, s)
+        bt.bt_forest_search(forest, d_desc, nbatches, dq, v, f, ws, wsb, 0, s)
     torch.cuda.synchronize()
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph):
-        bt.bt_forest_search(forest, d_desc, nbatches, dq, v, f, ws, wsb, 8, torch.cuda.current_stream())
+        bt.bt_forest_search(forest, d_desc, nbatches, dq, v, f, ws, wsb, 0, torch.cuda.current_stream())
     v.zero_()
     f.fill_(9)
     graph.replay()

@@ -46,10 +46,13 @@ def _trace(trees, nreq, seed, rate):
     return np.concatenate(keys), np.array(offs, np.uint64), sizes.astype(np.uint32), tids.astype(np.uint32), t
 
 
-@pytest.mark.parametrize("learned", [False, True])
+@pytest.mark.parametrize("learned", [False, True, "mixed"])
 def test_each_request_alone_equals_in_the_mix(bt, two_trees, learned):
     models = None
-    if learned:
+    if learned == "mixed":  # an MLP on one tree, the plain descent on the other
+        models = [bt.bt_model_train(two_trees[0][2].handle, bt.BT_MODEL_MLP, h_init=W.mlp_init_params(W.SEED_BASE + 5),
+                                    steps=200, batch=4096, lr=2e-3, seed=84), None]
+    elif learned:
         models = [bt.bt_model_train(t[2].handle, bt.BT_MODEL_PL, segments=64) for t in two_trees]
     srv = bt.bt_server_create([t[2] for t in two_trees], models, slots=4, max_batch=2048, deadline_us=50.0)
     keys, offs, sizes, tids, t = _trace(two_trees, 3000, seed=81, rate=2e5)
@@ -78,7 +81,8 @@ def test_each_request_alone_equals_in_the_mix(bt, two_trees, learned):
     bt.bt_server_destroy(srv)
     if models:
         for m in models:
-            bt.bt_model_free(m)
+            if m:
+                bt.bt_model_free(m)
 
 
 def test_memory_cap_and_back_pressure(bt, two_trees):
@@ -102,6 +106,27 @@ def test_memory_cap_and_back_pressure(bt, two_trees):
     with pytest.raises(bt.BTreeError) as e:
         bt.bt_server_submit(srv, 0, big, v, f)
     assert e.value.code == "BT_ERR_ARG"  # larger than the pending cap: never admissible
+    bt.bt_server_destroy(srv)
+
+
+def test_one_batch_serves_both_trees(bt, two_trees):
+    """A burst of requests to both trees, all waiting when the deadline
+    passes, is served by one multi-tree batch."""
+    srv = bt.bt_server_create([t[2] for t in two_trees], None, slots=2, max_batch=4096, deadline_us=20000.0)
+    keys, offs, sizes, tids, _ = _trace(two_trees, 60, seed=85, rate=1e6)
+    assert set(tids.tolist()) == {0, 1}
+    vals = np.zeros(keys.size, np.uint64)
+    found = np.zeros(keys.size, np.uint8)
+    for r in range(60):
+        o, c = int(offs[r]), int(sizes[r])
+        bt.bt_server_submit(srv, int(tids[r]), keys[o:o + c], vals[o:o + c], found[o:o + c])
+    bt.bt_server_drain(srv, 10.0)
+    st = bt.bt_server_get_stats(srv)
+    assert st.completed == 60 and st.batches == 1
+    for r in range(60):
+        o, c, tr = int(offs[r]), int(sizes[r]), int(tids[r])
+        ov, of, _, _ = two_trees[tr][3].search(keys[o:o + c])
+        assert np.array_equal(vals[o:o + c], ov) and np.array_equal(found[o:o + c], of)
     bt.bt_server_destroy(srv)
 
 
