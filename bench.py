@@ -44,10 +44,9 @@ L2_FLUSH_BYTES = 256 << 20
 # capture (dram__bytes_read.sum + dram__bytes_write.sum), valid only while
 # the kernel source is the one captured (sha256 prefix of csrc/search.cu).
 # DRAM bytes (read + write) of one k_descend launch on the default workload,
-# from the ncu capture summarised in profiles/k_descend_2p24keys_b2p20.md;
-# valid only while the descent's source (search.cu up to the end of
-# k_descend) hashes to the same value.
-NCU_DESCEND_TRAFFIC = {"descend_src_sha256": "", "bytes_per_launch": None}
+# from one ncu capture of it (summarised under profiles/); valid only while
+# the descent's source (desc_pipe.cu and descent.cuh) hashes to the same value.
+NCU_DESCEND_TRAFFIC = {"descend_src_sha256": "21015722eab4d033", "bytes_per_launch": 224089088}
 
 
 def parse_args(argv=None):
@@ -790,7 +789,7 @@ def batching_leg(a, bt, stream, nbatches: int = 10_000):
 
 # ------------------------------------------------------- serving leg
 
-def serving_leg(a, bt, rates=(1e6, 5e6, 20e6, 50e6), seconds: float = 0.25):
+def serving_leg(a, bt, rates=(1e6, 5e6, 20e6, 50e6, 100e6), seconds: float = 0.25):
     """Continuous batching under Poisson arrivals: 2 resident trees (1e6 and
     2e7 uint64 keys, fanout 32), requests of 1..64 lookups (geometric, mean
     8), 50 us batching deadline, memory-capped admission; plain search

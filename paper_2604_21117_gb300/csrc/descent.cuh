@@ -186,6 +186,22 @@ __device__ __forceinline__ Key32 key_shfl<Key32>(Key32 k, int src)
     return r;
 }
 
+// *p < key for a key read from global memory through L1; a 32-byte key's
+// first word alone unless it ties.
+template <typename K>
+__device__ __forceinline__ bool ld_lt(const K *p, const K &key)
+{
+    return ld_key(p) < key;
+}
+
+template <>
+__device__ __forceinline__ bool ld_lt<Key32>(const Key32 *p, const Key32 &key)
+{
+    const uint64_t w0 = __ldca(reinterpret_cast<const unsigned long long *>(p));
+    if (w0 != key.w[0]) return w0 < key.w[0];
+    return ld_key(p) < key;
+}
+
 // ------------------------------------------------------------- node math
 
 constexpr int kDescWarpsDefault = 8;
@@ -202,7 +218,7 @@ __device__ __forceinline__ int block_rank(const K *blk, K key)
     int r = 0;
 #pragma unroll
     for (int hlf = M / 2; hlf >= 1; hlf >>= 1)
-        if (blk[r + hlf - 1] < key) r += hlf;
+        if (mem_lt(blk + r + hlf - 1, key)) r += hlf;
     return r;
 }
 
@@ -221,7 +237,7 @@ __device__ __forceinline__ int block_rank_l1(const K *blk, K key)
     int r = 0;
 #pragma unroll
     for (int hlf = M / 2; hlf >= 1; hlf >>= 1)
-        if (ld_key(blk + r + hlf - 1) < key) r += hlf;
+        if (ld_lt(blk + r + hlf - 1, key)) r += hlf;
     return r;
 }
 

@@ -29,9 +29,12 @@ struct alignas(16) Key32 {
 
 __host__ __device__ __forceinline__ bool operator<(const Key32 &a, const Key32 &b)
 {
-    // the first unequal word decides, as the first unequal byte does
-    const bool e0 = a.w[0] == b.w[0], e1 = a.w[1] == b.w[1], e2 = a.w[2] == b.w[2];
-    return (a.w[0] < b.w[0]) | (e0 & ((a.w[1] < b.w[1]) | (e1 & ((a.w[2] < b.w[2]) | (e2 & (a.w[3] < b.w[3]))))));
+    // the first unequal word decides, as the first unequal byte does (distinct
+    // keys nearly always differ in the first word: one compare, no divergence)
+    if (a.w[0] != b.w[0]) return a.w[0] < b.w[0];
+    if (a.w[1] != b.w[1]) return a.w[1] < b.w[1];
+    if (a.w[2] != b.w[2]) return a.w[2] < b.w[2];
+    return a.w[3] < b.w[3];
 }
 
 __host__ __device__ __forceinline__ bool operator==(const Key32 &a, const Key32 &b)
@@ -73,6 +76,22 @@ struct KeyOps<Key32> {
 
 template <typename K>
 using RawOf = typename KeyOps<K>::Raw;
+
+// *p < key for a key in shared or global memory.  A 32-byte key's first word
+// is read alone, and the other three only when it ties.
+template <typename K>
+__device__ __forceinline__ bool mem_lt(const K *p, const K &key)
+{
+    return *p < key;
+}
+
+template <>
+__device__ __forceinline__ bool mem_lt<Key32>(const Key32 *p, const Key32 &key)
+{
+    const uint64_t w0 = p->w[0];
+    if (w0 != key.w[0]) return w0 < key.w[0];
+    return *p < key;
+}
 
 // One query of the partitioned batch: the key as the caller gave it, its
 // input position, and its local-sort digit (16 bytes for integer keys, 48

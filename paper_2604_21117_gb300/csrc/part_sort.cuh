@@ -23,9 +23,9 @@
 //   count     the slice's coarse buckets in shared memory, added to global
 //             totals with one atomic per bucket whose return value is the
 //             block's offset inside that bucket;
-//   scatter   bucket starts by a scan of the totals; every query takes its
-//             bucket's next position (a shared-memory atomic) and is written
-//             there as one record (key, input position, digit);
+//   scatter   bucket starts by a scan of the totals; every query goes to its
+//             block's run in its bucket, at its rank there (taken while
+//             counting), as one record (key, input position, digit);
 //   sort      groups of threads order the coarse buckets by digit, in
 //             place, several buckets per block at once.  Buckets of more
 //             than part_tile<K>() queries (a hot key, or a coarse bucket far
@@ -157,7 +157,7 @@ __device__ __forceinline__ uint32_t part_bucket(const PartSmem<K> &S, const Part
         uint32_t lo = S.R[j], hi = S.R[j + 1];
         while (lo < hi) {
             const uint32_t mid = (lo + hi) >> 1;
-            if (S.sp[mid] < q)
+            if (mem_lt(S.sp + mid, q))
                 lo = mid + 1;
             else
                 hi = mid;
@@ -167,7 +167,7 @@ __device__ __forceinline__ uint32_t part_bucket(const PartSmem<K> &S, const Part
         c = 0;
 #pragma unroll
         for (uint32_t h = (kSplitSlots + 1) / 2; h >= 1; h >>= 1)
-            if (S.sp[c + h - 1] < q) c += h;
+            if (mem_lt(S.sp + c + h - 1, q)) c += h;
     }
     if (pn.r == 0) return c >> pn.cshift;
     const K lo = c ? S.sp[c - 1] : pn.kmin;
@@ -201,7 +201,7 @@ __device__ __forceinline__ uint32_t part_bucket(const PartSmem<Key32> &S, const 
             uint32_t lo = S.R[j], hi = S.R[j + 1];
             while (lo < hi) {
                 const uint32_t mid = (lo + hi) >> 1;
-                if (S.sp[mid] < q)
+                if (mem_lt(S.sp + mid, q))
                     lo = mid + 1;
                 else
                     hi = mid;
@@ -211,7 +211,7 @@ __device__ __forceinline__ uint32_t part_bucket(const PartSmem<Key32> &S, const 
     } else {
 #pragma unroll
         for (uint32_t h = (kSplitSlots + 1) / 2; h >= 1; h >>= 1)
-            if (S.sp[c + h - 1] < q) c += h;
+            if (mem_lt(S.sp + c + h - 1, q)) c += h;
     }
     if (pn.r == 0) return c >> pn.cshift;
     const uint32_t top = (1u << pn.r) - 1u;
@@ -292,13 +292,14 @@ __host__ __device__ constexpr uint32_t part_cache()
 
 // Dynamic shared memory of k_partition for nb coarse buckets: the block's
 // counts / next positions (nb words), the bucket starts (nb + 4 words), then
-// an area holding first the cached slice (keys, then f) and later every
-// sort group's digit counters.
+// an area holding first the cached slice (keys, then f, then each query's
+// rank among the slice's queries of its bucket) and later every sort group's
+// digit counters.
 template <typename K>
 __host__ __device__ constexpr int part_area()
 {
-    return part_cache<K>() * static_cast<int>(sizeof(RawOf<K>) + 4) > kSortGroups * ((1 << kLocalBits) + 8) * 4
-               ? part_cache<K>() * static_cast<int>(sizeof(RawOf<K>) + 4)
+    return part_cache<K>() * static_cast<int>(sizeof(RawOf<K>) + 6) > kSortGroups * ((1 << kLocalBits) + 8) * 4
+               ? part_cache<K>() * static_cast<int>(sizeof(RawOf<K>) + 6)
                : kSortGroups * ((1 << kLocalBits) + 8) * 4;
 }
 
@@ -391,15 +392,18 @@ __device__ __forceinline__ void part_group_scan(uint32_t *cnt, uint32_t n, uint3
 
 // The whole partition in one cooperative launch; block g owns slice g of
 // the batch (ceil(nq / gridDim.x) queries).
-//   1. Count the slice's coarse buckets in shared memory (keeping each key
-//      and its f in shared memory when the slice fits part_cache).
+//   1. Count the slice's coarse buckets in shared memory (keeping each key,
+//      its f and its rank among the slice's queries of its bucket -- the
+//      counting atomic's return value -- in shared memory when the slice
+//      fits part_cache).
 //   2. Add every count to total[j] (nb words, zero on entry) with one atomic
 //      whose return value -- the bucket's queries counted by blocks whose
 //      atomic came first -- is the block's offset inside bucket j.
 //   -- grid barrier on total[nb] --
 //   3. Bucket starts: the exclusive scan of the totals (every block); the
 //      block's next position in bucket j is start[j] + offset[j].
-//   4. Every query of the slice takes its bucket's next position (a
+//   4. Every query of the slice goes to the block's next position in its
+//      bucket plus its rank (or, uncached, the bucket's next position from a
 //      shared-memory atomic) and is written there as one record.
 //   -- grid barrier on total[nb + 1] --
 //   5. Local sort, in place: groups of kSortThreads threads order the
@@ -422,6 +426,7 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_partition(const RawOf<K> *_
     unsigned char *area = reinterpret_cast<unsigned char *>(st + nb + 4);  // nb is a multiple of 4
     RawOf<K> *ck = reinterpret_cast<RawOf<K> *>(area);
     uint32_t *cf = reinterpret_cast<uint32_t *>(ck + part_cache<K>());
+    uint16_t *cr = reinterpret_cast<uint16_t *>(cf + part_cache<K>());
     part_load_tables(S, pn);
     for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x) cnt[j] = 0;
     __syncthreads();
@@ -445,10 +450,14 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_partition(const RawOf<K> *_
             if (i < ns) {
                 const uint32_t f = part_bucket(S, pn, KeyOps<K>::from_raw(key[u]));
                 if (cached) {
+                    // the query's rank in its bucket within the slice: its
+                    // place in the bucket's run, so the scatter needs no atomics
                     ck[i] = key[u];
                     cf[i] = f;
+                    cr[i] = static_cast<uint16_t>(atomicAdd(cnt + (f >> pn.lb), 1u));
+                } else {
+                    atomicAdd(cnt + (f >> pn.lb), 1u);
                 }
-                atomicAdd(cnt + (f >> pn.lb), 1u);
             }
         }
     }
@@ -504,7 +513,7 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_partition(const RawOf<K> *_
             const uint32_t i = i0 + u * blockDim.x;
             if (i < ns) {
                 if (!cached) f[u] = part_bucket(S, pn, KeyOps<K>::from_raw(key[u]));
-                const uint32_t pos = atomicAdd(cnt + (f[u] >> pn.lb), 1u);
+                const uint32_t pos = cached ? cnt[f[u] >> pn.lb] + cr[i] : atomicAdd(cnt + (f[u] >> pn.lb), 1u);
                 if (pos < nq) {  // always true when the counts agree; keeps a stray write in bounds
                     PartRec<K> r;
                     r.key = key[u];

@@ -281,3 +281,28 @@ def test_forest_autotune_keeps_the_fastest_correct_settings(bt):
     bt.bt_forest_search(forest, d_desc, nb, dq, v, f, ws, wsb)
     _check_forest(bt, oracles, desc, qs, v, f)
     bt.bt_forest_free(forest)
+
+
+def test_bad_work_list_entries_are_skipped_and_counted(bt):
+    """Entries naming a tree outside the forest or queries beyond the arrays
+    write nothing and are counted; the others are served."""
+    import torch
+    trees, oracles, desc, qs, allq, _ = _forest_case(bt, [5000, 50_000], [16, 32], 40, seed=97)
+    forest = bt.bt_forest_create(trees)
+    bt.bt_forest_bad_batches()  # clear
+    bad = desc.copy()
+    bad[3]["tree"] = 7                     # no such tree
+    bad[5]["offset"] = allq.size + 1000    # beyond the arrays
+    bad[6]["count"] = allq.size + 1        # runs past the end
+    v, f = _forest_outputs(bt, forest, bad, allq, torch.from_numpy(bad.view(np.uint8)).cuda())
+    assert bt.bt_forest_bad_batches() == 3
+    ff = f.cpu().numpy()
+    for b in (3, 5, 6):  # their own result ranges stay untouched
+        c, off = int(desc[b]["count"]), int(desc[b]["offset"])
+        assert (ff[off:off + c] == 9).all(), b
+    good = np.ones(desc.size, bool)
+    good[[3, 5, 6]] = False
+    keep = desc.copy()
+    keep["count"][~good] = 0
+    _check_forest(bt, oracles, keep, qs, v, f)
+    bt.bt_forest_free(forest)

@@ -172,3 +172,32 @@ def test_learned_small_trees_and_u32(bt, m, n):
 def pins_queries(keys):
     import pins
     return pins.probe_queries(keys, 32, W.rng(7), extra=300).astype(np.uint32)
+
+
+def test_training_is_what_narrows_the_window(bt):
+    """What the trained network gains over the untrained one on the same
+    tree: the error window that bounds the leaf search shrinks by far, and
+    the window (not the inner levels) then serves nearly every query."""
+    import torch
+    n, m = 400_000, 32
+    keys = W.lognormal_mixture_keys(n, seed=57)
+    vals = W.rank_values(n, 64)
+    tree = bt.BTree(keys, vals, m)
+    o = OracleTree(keys, vals, m)
+    L = int(tree.level_nodes[-1])
+    one = bt.bt_model_train(tree.handle, bt.BT_MODEL_MLP, h_init=W.mlp_init_params(58), steps=1, batch=16384,
+                            lr=2e-3, seed=59)
+    trained = bt.bt_model_train(tree.handle, bt.BT_MODEL_MLP, h_init=W.mlp_init_params(58), steps=1000,
+                                batch=16384, lr=2e-3, seed=59)
+    e1, e2 = bt.bt_model_get_info(one).max_err, bt.bt_model_get_info(trained).max_err
+    r1 = bt.bt_model_copy_err_bounds(one).astype(np.float64)
+    r2 = bt.bt_model_copy_err_bounds(trained).astype(np.float64)
+    assert e2 * 8 < e1 and e2 < L // 8, (e1, e2, L)
+    assert r2.mean() * 8 < r1.mean()  # the windows actually searched, per range of prediction
+    stats = torch.zeros(2, dtype=torch.int64, device="cuda")
+    _learned_check(bt, tree, o, trained, W.make_queries(keys, 1 << 17, 0.9, seed=60, width_bits=64), stats)
+    served, walked = (int(x) for x in stats.cpu().numpy())
+    assert served >= 0.95 * (served + walked)
+    bt.bt_model_free(one)
+    bt.bt_model_free(trained)
+    tree.close()
