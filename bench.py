@@ -382,14 +382,18 @@ DESIGNS = (
     ("synchronous cp.async (every level staged, waited)", dict(staging=0, inner=0, ballot=0, l2=0, lq=1)),
     ("synchronous bulk copy", dict(staging=1, inner=0, ballot=0, l2=0, lq=1)),
     ("synchronous, two queries per lane", dict(staging=0, inner=0, ballot=0, l2=0, lq=2)),
+    # not the paper's method: no sort, each warp takes 32 queries as they come
+    ("no sort: the batch as given, pipelined, inner through L1", dict(staging=2, inner=0, ballot=0, l2=64 << 20,
+                                                                      lq=1, sort_bits=0)),
 )
 
 
 def designs_leg(a, bt, tree, dq, out_v, out_f, ws, nb, stream, alg, pool, steps: int = 40):
-    """A/B of the descent designs on the same sorted batches: mean descent
-    and step time (CUDA events), and the descent's achieved GB/s of
-    algorithmic bytes; each design's results are checked against the
-    default design's on the last batch."""
+    """A/B of the descent designs on the same batches (sorted, except the
+    design that skips the sort): mean descent and step time (CUDA events),
+    and the descent's achieved GB/s of the sorted batch's algorithmic bytes;
+    each design's results are checked against the default design's on the
+    last batch."""
     import torch
     B = a.batch
     peak, _ = measured_peaks()
@@ -400,14 +404,15 @@ def designs_leg(a, bt, tree, dq, out_v, out_f, ws, nb, stream, alg, pool, steps:
         bt.bt_tree_set_lane_queries(tree.handle, d["lq"])
         bt.bt_tree_set_descent(tree.handle, d["inner"], d["ballot"])
         bt.bt_tree_set_l2_window(tree.handle, d["l2"])
+        sb = d.get("sort_bits", a.sort_bits)
         for i in range(3):
-            bt.bt_search_batch_ex(tree.handle, dq[i % pool], B, out_v, out_f, ws, nb, a.sort_bits, None, stream)
+            bt.bt_search_batch_ex(tree.handle, dq[i % pool], B, out_v, out_f, ws, nb, sb, None, stream)
         ev = []
         for i in range(steps):
             e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
             e[1].record(stream)  # create it; recorded again inside the call
             e[0].record(stream)
-            bt.bt_search_batch_ex(tree.handle, dq[i % pool], B, out_v, out_f, ws, nb, a.sort_bits, None, stream, e[1])
+            bt.bt_search_batch_ex(tree.handle, dq[i % pool], B, out_v, out_f, ws, nb, sb, None, stream, e[1])
             e[2].record(stream)
             ev.append(e)
         torch.cuda.synchronize()
@@ -907,7 +912,10 @@ def run_ours(a):
 
     K = a.steps
 
-    def timed_loop(clear):
+    def timed_loop(clear, phases=True):
+        # phases: also record an event between the partition and the descent
+        # (it keeps the descent from starting under the partition's tail, so
+        # the step itself is timed without it)
         ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
         for e in ev:  # create the events (the middle one is recorded inside the call)
             for x in e:
@@ -919,14 +927,16 @@ def run_ours(a):
             clear(i)
             e0, e1, e2 = ev[i]
             e0.record(stream)
-            step(i, e1)
+            step(i, e1 if phases else None)
             e2.record(stream)
         torch.cuda.synchronize()
         barrier(world)
-        return ([e[0].elapsed_time(e[2]) for e in ev], [e[0].elapsed_time(e[1]) for e in ev],
-                [e[1].elapsed_time(e[2]) for e in ev], time.perf_counter() - w0)
+        return ([e[0].elapsed_time(e[2]) for e in ev], [e[0].elapsed_time(e[1]) for e in ev] if phases else None,
+                [e[1].elapsed_time(e[2]) for e in ev] if phases else None, time.perf_counter() - w0)
 
-    step_ms, sort_ms, desc_ms, wall = timed_loop(clear_l2)
+    step_ms, _, _, wall = timed_loop(clear_l2, phases=False)
+    # the same steps with the phase event, for the partition / descent split
+    phase_step_ms, sort_ms, desc_ms, _ = timed_loop(clear_l2)
     total_s = sum(step_ms) / 1e3
     total_s_max = reduce_max(total_s, world, device="cuda")
     value = B * K * world / total_s_max
@@ -987,7 +997,11 @@ def run_ours(a):
                                   "rotate"}[a.l2]},
         "p50_us": 1e3 * sdev[len(sdev) // 2], "p99_us": 1e3 * sdev[min(len(sdev) - 1, int(0.99 * len(sdev)))],
         "iqm_us": 1e3 * iqm(step_ms),
-        "phase_ms": {"sort": statistics.fmean(sort_ms), "descend": statistics.fmean(desc_ms)},
+        "phase_ms": {"sort": statistics.fmean(sort_ms), "descend": statistics.fmean(desc_ms),
+                     "step_with_phase_event": statistics.fmean(phase_step_ms),
+                     "note": "from a second pass of the same steps with an event between the phases; the "
+                             "timed step (value, ms_per_step) has none, so its descent may start under the "
+                             "partition's tail"},
         "hbm_gbs": step_gbs,
         "roofline": {"kernel": "k_descend (level-wise descent + leaf probe + scatter)", "bound": "hbm",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
