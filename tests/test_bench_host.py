@@ -199,3 +199,9 @@ def test_range_split_routes_by_part_ranges():
             lo, hi = RS.part_bounds(keys.size, parts, p)
             assert np.all(dest[lo:hi] == p)  # every stored key routes to the part that holds it
         assert RS.route(np.array([0, 2**64 - 1], np.uint64), split).tolist() == [0, parts - 1]
+
+
+def test_profile_cases_usage_without_a_case():
+    from paper_2604_21117_gb300 import profile_cases
+    assert profile_cases.main([]) == 2
+    assert profile_cases.main(["nothing"]) == 2

@@ -23,14 +23,14 @@ def bt():
     return btree
 
 
-def _forest_case(bt, sizes, fanouts, nbatches, seed, kw=64):
+def _forest_case(bt, sizes, fanouts, nbatches, seed, kw=64, vw=64):
     import torch
     trees, oracles, keysets = [], [], []
     for i, (n, m) in enumerate(zip(sizes, fanouts)):
         keys = W.uniform_keys(n, kw, seed=seed + i) if n else np.empty(0, W.key_dtype(kw))
-        vals = W.rank_values(n, 64)
+        vals = W.rank_values(n, vw)
         trees.append(bt.BTree(keys, vals, m))
-        oracles.append(OracleTree(keys, vals, m))
+        oracles.append(OracleTree(keys, vals, m, val_bits=vw))
         keysets.append(keys)
     g = W.rng(seed)
     counts = W.log_uniform_batch_sizes(nbatches, seed=seed + 100)
@@ -176,10 +176,10 @@ def test_two_queries_per_lane(bt, m, kw, vw, nq):
         assert np.array_equal(v.cpu().numpy().astype(np.uint64), ov) and np.array_equal(f.cpu().numpy(), of), sb
 
 
-def _forest_outputs(bt, forest, desc, allq, d_desc, warps=0):
+def _forest_outputs(bt, forest, desc, allq, d_desc, warps=0, vw=64):
     import torch
     nb = desc.size
-    v = torch.zeros(max(1, allq.size), dtype=torch.uint64, device="cuda")
+    v = torch.zeros(max(1, allq.size), dtype=torch.uint64 if vw == 64 else torch.uint32, device="cuda")
     f = torch.full((max(1, allq.size),), 9, dtype=torch.uint8, device="cuda")
     wsb = bt.bt_forest_workspace_bytes(nb)
     ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
@@ -306,3 +306,21 @@ def test_bad_work_list_entries_are_skipped_and_counted(bt):
     keep["count"][~good] = 0
     _check_forest(bt, oracles, keep, qs, v, f)
     bt.bt_forest_free(forest)
+
+
+@pytest.mark.parametrize("kw,vw", [(32, 32), (32, 64), (64, 32)])
+@pytest.mark.parametrize("learned", [False, True])
+def test_forest_every_key_and_value_width(bt, kw, vw, learned):
+    """The four kernel instantiations (key x value width), plain and learned,
+    at two queries per lane and at one."""
+    trees, oracles, desc, qs, allq, d_desc = _forest_case(bt, [3000, 200_000, 40], [16, 32, 8], 300, seed=98,
+                                                          kw=kw, vw=vw)
+    models = [bt.bt_model_train(t.handle, bt.BT_MODEL_PL, segments=64) for t in trees] if learned else None
+    forest = bt.bt_forest_create_learned(trees, models) if learned else bt.bt_forest_create(trees)
+    for lq in (1, 2):
+        bt.bt_forest_set_launch(forest, 8, 16384, lq, 0)
+        v, f = _forest_outputs(bt, forest, desc, allq, d_desc, vw=vw)
+        _check_forest(bt, oracles, desc, qs, v, f)
+    bt.bt_forest_free(forest)
+    for m in models or ():
+        bt.bt_model_free(m)

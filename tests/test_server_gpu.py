@@ -139,3 +139,34 @@ def test_batches_overlap_on_the_device(bt, two_trees):
     st = bt.bt_server_get_stats(srv)
     assert st.completed == 4000 and st.max_inflight >= 2
     bt.bt_server_destroy(srv)
+
+
+def test_many_trees_and_32_bit_keys(bt):
+    """40 trees of 32-bit keys and values: a batch's work list (up to two
+    entries per tree) no longer fits the kernel's shared-memory copy and is
+    read from host-mapped memory; every request equals its tree's oracle."""
+    trees = []
+    for i in range(40):
+        n = 50 + 997 * i
+        keys = W.uniform_keys(n, 32, seed=300 + i)
+        vals = W.rank_values(n, 32)
+        trees.append((keys, vals, bt.BTree(keys, vals, 16), OracleTree(keys, vals, 16, val_bits=32)))
+    srv = bt.bt_server_create([t[2] for t in trees], None, slots=4, max_batch=4096, deadline_us=2000.0)
+    g = W.rng(87)
+    nreq = 2000
+    tids = g.integers(0, 40, size=nreq)
+    sizes = W.geometric_request_sizes(nreq, seed=88)
+    reqs = []
+    for r in range(nreq):
+        q = W.make_queries(trees[tids[r]][0], int(sizes[r]), 0.8, seed=400 + r, width_bits=32)
+        v = np.zeros(q.size, np.uint32)
+        f = np.full(q.size, 9, np.uint8)
+        bt.bt_server_submit(srv, int(tids[r]), q, v, f)
+        reqs.append((int(tids[r]), q, v, f))
+    bt.bt_server_drain(srv, 30.0)
+    st = bt.bt_server_get_stats(srv)
+    assert st.completed == nreq
+    for tr, q, v, f in reqs:
+        ov, of, _, _ = trees[tr][3].search(q)
+        assert np.array_equal(v.astype(np.uint64), ov) and np.array_equal(f, of)
+    bt.bt_server_destroy(srv)
