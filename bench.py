@@ -6,7 +6,12 @@ fanout 32, uint64 rank values; batches of 2^20 point lookups at 90% hits
 (uniform).  One step = one pass of the whole search path over one batch:
 the on-device partition of the batch by key, then the level-wise descent, leaf
 probe and scatter to input order.  Inputs are resident in HBM when a step
-starts.  By default the L2 is not flushed between steps: the 282 MB tree is
+starts.  By default two steps are in flight: steps alternate between two
+streams, each with its own workspace and outputs, and the tree's launch
+shapes are capped (bt_tree_set_corun) so that one batch's partition runs
+beside the previous batch's descent; the same steps one at a time on one
+stream are reported beside it (``one_stream``).  By default the L2 is not
+flushed between steps: the 282 MB tree is
 larger than the 129 MB L2 and four batches rotate, so a step finds its batch
 evicted and only the hot upper tree levels cached, as in steady serving;
 the same loop with a 256 MB buffer overwritten before every step is
@@ -61,6 +66,12 @@ def parse_args(argv=None):
     p.add_argument("--hit", type=float, default=0.9)
     p.add_argument("--zipf", type=float, default=None)
     p.add_argument("--sort-bits", type=int, default=-1)
+    p.add_argument("--streams", type=int, choices=[1, 2], default=2,
+                   help="steps in flight: 2 alternates two streams (each with its own workspace and "
+                        "outputs), so one batch's partition runs beside the previous batch's descent")
+    p.add_argument("--corun", default="0,1",
+                   help="resident blocks per SM of the descent and the partition with --streams 2 "
+                        "(0 = as many as fit)")
     p.add_argument("--l2", choices=["write", "read", "none"], default="none",
                    help="between timed steps: nothing (default: the 282 MB tree already exceeds the L2 and "
                         "the batches rotate), overwrite a 256 MB buffer, or read one")
@@ -934,12 +945,57 @@ def run_ours(a):
         return ([e[0].elapsed_time(e[2]) for e in ev], [e[0].elapsed_time(e[1]) for e in ev] if phases else None,
                 [e[1].elapsed_time(e[2]) for e in ev] if phases else None, time.perf_counter() - w0)
 
-    step_ms, _, _, wall = timed_loop(clear_l2, phases=False)
-    # the same steps with the phase event, for the partition / descent split
+    # the second stream's workspace and outputs
+    ws2 = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    out_v2 = torch.empty(B, dtype=torch.uint64, device="cuda")
+    out_f2 = torch.empty(B, dtype=torch.uint8, device="cuda")
+    bufs = [(out_v, out_f, ws), (out_v2, out_f2, ws2)]
+    pstreams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    corun = tuple(int(x) for x in a.corun.split(","))
+
+    def pipelined_loop():
+        # step i on stream i % 2 with buffer set i % 2; the total runs from an
+        # event on stream 0 (stream 1 waits for it) to stream 0's join of stream 1
+        per = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier(world)
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        t0e.record(pstreams[0])
+        pstreams[1].wait_event(t0e)
+        for i in range(K):
+            st, (ov, of, w) = pstreams[i % 2], bufs[i % 2]
+            with torch.cuda.stream(st):
+                clear_l2(i)
+            per[i][0].record(st)
+            bt.bt_search_batch_ex(tree.handle, dq[i % pool], B, ov, of, w, nb, sort_bits, None, st)
+            per[i][1].record(st)
+        pstreams[0].wait_stream(pstreams[1])
+        t1e.record(pstreams[0])
+        torch.cuda.synchronize()
+        barrier(world)
+        return t0e.elapsed_time(t1e), [e0.elapsed_time(e1) for e0, e1 in per], time.perf_counter() - w0
+
+    # one stream, nothing capped: each step alone (and the phase split)
+    one_ms, _, _, one_wall = timed_loop(clear_l2, phases=False)
     phase_step_ms, sort_ms, desc_ms, _ = timed_loop(clear_l2)
-    total_s = sum(step_ms) / 1e3
+    if a.streams == 2:
+        bt.bt_tree_set_corun(tree.handle, corun[0], corun[1])
+        for i in range(a.warmup):  # warm up the capped launch shapes on both streams
+            st, (ov, of, w) = pstreams[i % 2], bufs[i % 2]
+            bt.bt_search_batch_ex(tree.handle, dq[i % pool], B, ov, of, w, nb, sort_bits, None, st)
+        torch.cuda.synchronize()
+        total_ms, step_ms, wall = pipelined_loop()
+        bt.bt_tree_set_corun(tree.handle, 0, 0)
+        last_out = bufs[(K - 1) % 2]
+    else:
+        total_ms, step_ms, wall = sum(one_ms), one_ms, one_wall
+        last_out = bufs[0]
+    total_s = total_ms / 1e3
     total_s_max = reduce_max(total_s, world, device="cuda")
     value = B * K * world / total_s_max
+    one_total_max = reduce_max(sum(one_ms) / 1e3, world, device="cuda")
+    out_v, out_f = last_out[0], last_out[1]
 
     # correctness spot check of the last step against the plain definition
     if world > 1:
@@ -972,7 +1028,7 @@ def run_ours(a):
             and a.staging == 2 and a.inner in (1, 2) and a.ballot == 0 and a.l2_window == 64 << 20 and a.warps <= 0
             and a.pin < 0 and a.sort_bits < 0):
         traffic = NCU_DESCEND_TRAFFIC["bytes_per_launch"]
-    step_gbs = statistics.fmean(node_bytes) / (statistics.fmean(step_ms) / 1e3) / 1e9
+    step_gbs = statistics.fmean(node_bytes) / (total_s / K) / 1e9  # per batch, at the whole job's rate
     sort_k = bt.bt_sort_launches(tree.handle, B, sort_bits)
     # our kernels per step: the partition's kernels, then the descent
     launches_per_step = sort_k + 1
@@ -980,7 +1036,7 @@ def run_ours(a):
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
-        "warmup": a.warmup, "ms_per_step": statistics.fmean(step_ms), "higher_is_better": True,
+        "warmup": a.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64",
         "data": "synthetic (seeded uniform keys and query mix)",
         "config": workload_config(a, world),
@@ -991,17 +1047,24 @@ def run_ours(a):
                                     2: "staged (cp.async) for partitioned batches, else through L1"}[a.inner],
                    "leaf_rank": "ballot + popc" if a.ballot else "binary search",
                    "l2_window_bytes": a.l2_window, "lane_queries": a.lane_queries,
+                   "steps_in_flight": a.streams,
+                   "corun_blocks_per_sm": ({"descent": corun[0], "partition": corun[1]} if a.streams == 2
+                                           else None),
                    "l2": {"write": "flushed before every timed step (256 MB device write)",
                           "read": "flushed before every timed step (256 MB device read)",
                           "none": "not flushed: the 282 MB tree exceeds the 129 MB L2 and 4 batches "
                                   "rotate"}[a.l2]},
         "p50_us": 1e3 * sdev[len(sdev) // 2], "p99_us": 1e3 * sdev[min(len(sdev) - 1, int(0.99 * len(sdev)))],
         "iqm_us": 1e3 * iqm(step_ms),
+        "latency_note": ("p50/p99/iqm: each step's own time on its stream, with the other stream's step "
+                         "running beside it" if a.streams == 2 else "each step alone"),
+        "one_stream": {"value": B * K * world / one_total_max, "ms_per_step": statistics.fmean(one_ms),
+                       "p50_us": 1e3 * sorted(one_ms)[len(one_ms) // 2],
+                       "note": "the same steps one at a time on one stream, launch shapes uncapped"},
         "phase_ms": {"sort": statistics.fmean(sort_ms), "descend": statistics.fmean(desc_ms),
                      "step_with_phase_event": statistics.fmean(phase_step_ms),
-                     "note": "from a second pass of the same steps with an event between the phases; the "
-                             "timed step (value, ms_per_step) has none, so its descent may start under the "
-                             "partition's tail"},
+                     "note": "one stream, launch shapes uncapped, an event between the phases (which keeps "
+                             "the descent from starting under the partition's tail)"},
         "hbm_gbs": step_gbs,
         "roofline": {"kernel": "k_descend (level-wise descent + leaf probe + scatter)", "bound": "hbm",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -1010,7 +1073,7 @@ def run_ours(a):
                      "distinct_nodes_per_level": alg[0][0], "distinct_value_sectors": alg[0][1],
                      # the whole search per batch (sort + descent): bytes of the distinct
                      # nodes the batch touches (and its value sectors) over the step time
-                     "per_batch": {"what": "distinct node bytes + value sectors per batch / whole-step time",
+                     "per_batch": {"what": "distinct node bytes + value sectors per batch / (whole job time / steps)",
                                    "bytes": statistics.fmean(node_bytes), "achieved": step_gbs,
                                    "frac": step_gbs / peak},
                      "target": {"frac": 0.5, "applies_to": "per_batch (the whole search, sort included)",
@@ -1091,6 +1154,8 @@ def run_ours(a):
                          torch.empty(B, dtype=torch.uint64).pin_memory(),
                          torch.empty(B, dtype=torch.uint8).pin_memory(),
                          torch.empty(nbh, dtype=torch.uint8, device="cuda")))
+        if a.streams == 2:  # the same launch-shape caps as the device-resident pipelined loop
+            bt.bt_tree_set_corun(tree.handle, corun[0], corun[1])
         for j in range(4):
             h = bufs[j % 2]
             bt.bt_search_batch_host(tree.handle, h[0], B, h[1], h[2], h[3], nbh, streams[j % 2])
@@ -1112,9 +1177,12 @@ def run_ours(a):
         torch.cuda.synchronize()
         pipe_s = reduce_max(p0.elapsed_time(p1) / 1e3, world, device="cuda")
         pipelined = B * Ke * world / pipe_s
+        bt.bt_tree_set_corun(tree.handle, 0, 0)
         line["e2e"] = {"value": pipelined, "unit": UNIT, "h2d_bytes_per_step": B * kb,
                        "d2h_bytes_per_step": B * (vb + 1), "steps": Ke,
-                       "entry_point": "bt_search_batch_host (pinned host buffers), two streams alternating",
+                       "entry_point": "bt_search_batch_host (pinned host buffers), two streams alternating"
+                                      + (f", launch shapes capped at {corun[0]} descent / {corun[1]} partition "
+                                         "blocks per SM" if a.streams == 2 else ""),
                        "serial_value": serial, "serial_p50_us": 1e3 * sorted(tt)[len(tt) // 2],
                        "l2": "serial: flushed before every step; pipelined: not flushed (steps overlap; the "
                              "282 MB tree exceeds the 129 MB L2)"}

@@ -489,6 +489,20 @@ bt_status bt_tree_set_descent(bt_tree *tree, uint32_t inner_staged, uint32_t ran
  * Errors: BT_ERR_ARG, BT_ERR_CUDA. */
 bt_status bt_tree_set_l2_window(bt_tree *tree, uint64_t max_bytes);
 
+/* Batches in flight side by side: at most descent_blocks_per_sm resident
+ * blocks of the tree's descent and partition_blocks_per_sm of its partition
+ * on every SM (0: as many as fit, the default).  With the partition at one
+ * block per SM (descent_blocks_per_sm 0, partition_blocks_per_sm 1 with the
+ * default launch settings), a caller that alternates two streams -- each
+ * with its own workspace and outputs -- gets batch i+1's partition running
+ * beside batch i's descent: the paper's pipelining of successive batches
+ * (Sec. V-B, Fig. 7), here on the device.  Results do not change; a single
+ * stream runs slower with the caps.  The partition stays one cooperative
+ * launch (all of its blocks resident before any passes a grid barrier).
+ * Not thread-safe with searches running on the tree.  No counterpart in
+ * the paper's kernel.  BT_ERR_ARG above 32. */
+bt_status bt_tree_set_corun(bt_tree *tree, uint32_t descent_blocks_per_sm, uint32_t partition_blocks_per_sm);
+
 /* Test hook: poll limit of the first bounded wait of the descents' bulk-copy
  * staging, BT_DEFAULT_WAIT_POLLS unless changed; 0 makes every such wait
  * give up at once.  After a wait gives up, the warp counts it

@@ -38,7 +38,7 @@ EXPORTED = ("bt_build", "bt_free", "bt_tree_info", "bt_tree_copy_image", "bt_sea
             "bt_learned_descend_sorted", "bt_learned_search_batch", "bt_model_copy_err_bounds",
             "bt_forest_create", "bt_forest_create_learned", "bt_forest_free", "bt_forest_set_launch",
             "bt_forest_get_launch", "bt_forest_autotune", "bt_forest_workspace_bytes", "bt_forest_search", "bt_forest_bad_batches", "bt_tree_set_launch", "bt_tree_set_staging",
-            "bt_tree_set_lane_queries", "bt_tree_set_descent", "bt_tree_set_l2_window", "bt_debug_set_wait_polls",
+            "bt_tree_set_lane_queries", "bt_tree_set_descent", "bt_tree_set_l2_window", "bt_tree_set_corun", "bt_debug_set_wait_polls",
             "bt_check_timeouts", "bt_autotune", "bt_paper_node_bytes", "bt_paper_layout_build",
             "bt_paper_search_batch", "bt_paper_descend_sorted",
             "bt_server_create", "bt_server_submit", "bt_server_poll", "bt_server_drain", "bt_server_get_stats",
@@ -396,6 +396,8 @@ _lib.bt_tree_set_descent.restype = _i
 _lib.bt_tree_set_descent.argtypes = [_vp, ctypes.c_uint32, ctypes.c_uint32]
 _lib.bt_tree_set_l2_window.restype = _i
 _lib.bt_tree_set_l2_window.argtypes = [_vp, _u64]
+_lib.bt_tree_set_corun.restype = _i
+_lib.bt_tree_set_corun.argtypes = [_vp, ctypes.c_uint32, ctypes.c_uint32]
 _lib.bt_debug_set_wait_polls.restype = None
 _lib.bt_debug_set_wait_polls.argtypes = [ctypes.c_uint32]
 _lib.bt_check_timeouts.restype = _i
@@ -493,6 +495,11 @@ def bt_tree_set_lane_queries(tree: int, per_lane: int) -> None:
 
 def bt_tree_set_descent(tree: int, inner_staged: int = 0, rank_ballot: int = 0) -> None:
     _check("bt_tree_set_descent", _lib.bt_tree_set_descent(tree, inner_staged, rank_ballot))
+
+
+def bt_tree_set_corun(tree: int, descent_blocks_per_sm: int, partition_blocks_per_sm: int) -> None:
+    """Resident blocks per SM of the descent and the partition (0 = as many as fit)."""
+    _check("bt_tree_set_corun", _lib.bt_tree_set_corun(tree, descent_blocks_per_sm, partition_blocks_per_sm))
 
 
 def bt_tree_set_l2_window(tree: int, max_bytes: int) -> None:

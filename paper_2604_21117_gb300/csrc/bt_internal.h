@@ -39,6 +39,11 @@ struct DevTree {
     int inner_stage;     // pipelined descent: inner levels through L1 (0), staged with cp.async (1), or
                          // staged for partitioned batches and through L1 otherwise (2)
     int rank_ballot;     // pipelined descent: leaf rank by binary search (0) or warp ballot + popc (1)
+    // Resident blocks per SM at most (0: as many as fit) of the descent and
+    // of the partition, so that one batch's partition can run beside the
+    // previous batch's descent (bt_tree_set_corun).
+    int corun_descent_bps;
+    int corun_partition_bps;
     // Splitters of the batch partition: the largest keys of nsplit evenly
     // spaced leaves, and nsplit + 1 reciprocal widths of the key segments
     // they bound (part_sort.cuh).

@@ -188,6 +188,14 @@ extern "C" bt_status bt_tree_set_descent(bt_tree *t, uint32_t inner_staged, uint
     return BT_OK;
 }
 
+extern "C" bt_status bt_tree_set_corun(bt_tree *t, uint32_t descent_blocks_per_sm, uint32_t partition_blocks_per_sm)
+{
+    if (!t || descent_blocks_per_sm > 32 || partition_blocks_per_sm > 32) return BT_ERR_ARG;
+    t->dev.corun_descent_bps = static_cast<int>(descent_blocks_per_sm);
+    t->dev.corun_partition_bps = static_cast<int>(partition_blocks_per_sm);
+    return BT_OK;
+}
+
 extern "C" bt_status bt_tree_set_l2_window(bt_tree *t, uint64_t max_bytes)
 {
     if (!t) return BT_ERR_ARG;
@@ -339,6 +347,8 @@ extern "C" bt_status bt_build(const void *h_keys, const void *h_vals, uint64_t n
     d.lane_queries = 1;
     d.staging = BT_STAGE_PIPELINED;
     d.inner_stage = 2;  // staged for partitioned batches, through L1 otherwise
+    d.corun_descent_bps = 0;
+    d.corun_partition_bps = 0;
     set_pin_levels(d, t->info, 16384);
 
     // Shape arithmetic: children (or keys, for leaves) per node.

@@ -496,7 +496,7 @@ static cudaError_t launch_pipe(const DescendArgs &a, cudaStream_t s)
     if (e != cudaSuccess) return e;
     unsigned grid = 0;
     e = persistent_grid(reinterpret_cast<const void *>(kern), nw * 32, smem, static_cast<uint64_t>(nw) * 32, a.nq,
-                        &grid);
+                        &grid, t.corun_descent_bps);
     if (e != cudaSuccess) return e;
     return launch_with_window(kern, grid, nw * 32, smem, s, a.tree, t, static_cast<const RawOf<K> *>(a.q), a.qidx,
                               static_cast<const PartRec<K> *>(a.recs), a.nq, static_cast<V *>(a.out_v), a.out_f,

@@ -333,7 +333,8 @@ static cudaError_t launch_sync(const DescendArgs &a, cudaStream_t s)
     cudaError_t e = ensure_dyn_smem(kern, kPinBudgetMax + kDescWarpsMax * sync_smem_per_warp<K, M>());
     if (e != cudaSuccess) return e;
     unsigned grid = 0;
-    e = persistent_grid(kern, nw * 32, smem, static_cast<uint64_t>(nw) * (two ? 64 : 32), a.nq, &grid);
+    e = persistent_grid(kern, nw * 32, smem, static_cast<uint64_t>(nw) * (two ? 64 : 32), a.nq, &grid,
+                        t.corun_descent_bps);
     if (e != cudaSuccess) return e;
     if (two)
         k_descend2<K, V, M, COUNT><<<grid, nw * 32, smem, s>>>(t, static_cast<const RawOf<K> *>(a.q), a.qidx,

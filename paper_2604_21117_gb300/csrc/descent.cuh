@@ -315,7 +315,7 @@ cudaError_t descend_paper_layout(const DevTree &t, const PaperTree &p, const voi
 // Grid of a persistent descent: enough blocks for the chunks, at most one
 // full wave of resident blocks.
 cudaError_t persistent_grid(const void *kern, int threads, int smem, uint64_t units_per_block, uint64_t units,
-                            unsigned *grid);
+                            unsigned *grid, int max_per_sm = 0);
 
 // This translation unit's wait counters, read and cleared (synchronous).
 static inline cudaError_t take_wait_counters(unsigned *timeouts, unsigned *pending)

@@ -29,12 +29,13 @@
 namespace btgb {
 
 cudaError_t persistent_grid(const void *kern, int threads, int smem, uint64_t units_per_block, uint64_t units,
-                            unsigned *grid)
+                            unsigned *grid, int max_per_sm)
 {
     int per_sm = 0, sms = 0;
     cudaError_t e = blocks_per_sm(kern, threads, smem, &per_sm);
     if (e == cudaSuccess) e = dev_sm_count(&sms);
     if (e != cudaSuccess) return e;
+    if (max_per_sm > 0 && max_per_sm < per_sm) per_sm = max_per_sm;
     uint64_t g = (units + units_per_block - 1) / units_per_block;
     const uint64_t cap = static_cast<uint64_t>(sms) * static_cast<uint64_t>(per_sm);
     if (g > cap) g = cap;
@@ -206,6 +207,7 @@ static cudaError_t part_sort(const DevTree &t, const RawOf<K> *q, uint64_t nq, c
     // one slice per block, at least kPartPerBlock queries each, every block
     // resident (the kernel's grid barriers need all of them)
     uint64_t g = (nq + kPartPerBlock - 1) / kPartPerBlock;
+    if (t.corun_partition_bps > 0 && t.corun_partition_bps < occ) occ = t.corun_partition_bps;
     const uint64_t cap = static_cast<uint64_t>(occ) * static_cast<uint64_t>(sms);
     if (g > cap) g = cap;
     if (g > kMaxPartBlocks) g = kMaxPartBlocks;

@@ -161,3 +161,16 @@ def test_range_build_rejects_bad_arguments_before_touching_the_gpu(bt):
     assert lib.bt_range_build(keys.ctypes.data, keys.ctypes.data, 10, 32, 8, 16, 2, None, ctypes.byref(out)) == 1
     assert lib.bt_range_workspace_bytes(None, 100) == 0
     assert lib.bt_range_part(None, 0) is None
+
+
+def test_corun_caps_check_their_range(bt):
+    # an empty tree is built without a device; the setter only stores the caps
+    h = bt.bt_build(np.empty(0, np.uint64), np.empty(0, np.uint64), 32, stream=0)
+    bt.bt_tree_set_corun(h, 3, 1)
+    bt.bt_tree_set_corun(h, 0, 0)
+    for d, p in ((33, 1), (3, 33)):
+        with pytest.raises(bt.BTreeError) as e:
+            bt.bt_tree_set_corun(h, d, p)
+        assert e.value.code == "BT_ERR_ARG"
+    assert bt._lib.bt_tree_set_corun(None, 3, 1) == 1
+    bt.bt_free(h)

@@ -119,3 +119,38 @@ def test_bounded_wait_gives_up_and_is_reported(bt, staging):
     assert e.value.code == "BT_ERR_TIMEOUT"
     _same(tree, o, q)
     bt.bt_check_timeouts()  # nothing new
+
+
+@pytest.mark.parametrize("caps", [(3, 1), (2, 1), (1, 1)])
+def test_two_streams_with_corun_caps(bt, caps):
+    """Steps alternating between two streams, each with its own workspace and
+    outputs, with the descent and partition capped so that they run side by
+    side: every step's results equal the oracle's."""
+    import torch
+    n, m, B = 300_000, 32, 70_001
+    keys = W.uniform_keys(n, 64, seed=131)
+    vals = W.rank_values(n, 64)
+    tree = bt.BTree(keys, vals, m)
+    o = OracleTree(keys, vals, m)
+    bt.bt_tree_set_corun(tree.handle, *caps)
+    qs = [W.make_queries(keys, B, 0.9, seed=132 + i, width_bits=64) for i in range(4)]
+    want = [o.search(q)[:2] for q in qs]
+    nb = tree.workspace_bytes(B)
+    bufs = [(torch.empty(nb, dtype=torch.uint8, device="cuda"), torch.empty(B, dtype=torch.uint64, device="cuda"),
+             torch.empty(B, dtype=torch.uint8, device="cuda")) for _ in range(2)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    dq = [torch.from_numpy(q).cuda() for q in qs]
+    torch.cuda.synchronize()
+    got = []
+    for i in range(8):
+        ws, v, f = bufs[i % 2]
+        bt.bt_search_batch(tree.handle, dq[i % 4], B, v, f, ws, nb, streams[i % 2])
+        if i >= 6:  # the last two steps, one on each stream
+            streams[i % 2].synchronize()
+            got.append((i % 4, v.cpu().numpy().copy(), f.cpu().numpy().copy()))
+    torch.cuda.synchronize()
+    bt.bt_check_timeouts()
+    for qi, v, f in got:
+        assert np.array_equal(v, want[qi][0]) and np.array_equal(f, want[qi][1])
+    bt.bt_tree_set_corun(tree.handle, 0, 0)
+    tree.close()
