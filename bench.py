@@ -51,7 +51,7 @@ L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) of one k_descend launch on the default workload,
 # from one ncu capture of it (summarised under profiles/); valid only while
 # the descent's source (desc_pipe.cu and descent.cuh) hashes to the same value.
-NCU_DESCEND_TRAFFIC = {"descend_src_sha256": "21015722eab4d033", "bytes_per_launch": 224089088}
+NCU_DESCEND_TRAFFIC = {"descend_src_sha256": "5a7a4ccffe096dcb", "bytes_per_launch": 223773184}
 
 
 def parse_args(argv=None):
