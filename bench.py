@@ -1143,46 +1143,43 @@ def run_ours(a):
         e2e_s = reduce_max(sum(tt) / 1e3, world, device="cuda")
         serial = B * Ke * world / e2e_s
         # the same calls pipelined the way a host keeps a GPU busy (Sec. V-B,
-        # Fig. 7): two streams, each with its own pinned buffers and
-        # workspace, steps issued alternately, so one step's copies overlap
-        # the other's kernels; every step still copies its queries in and its
-        # values and found flags out.
-        streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+        # Fig. 7): three streams, each with its own pinned buffers and
+        # workspace, steps issued in turn, so one step's copies in, another's
+        # copies out and a third's kernels overlap (the host link, not the
+        # search, bounds this path); every step still copies its queries in
+        # and its values and found flags out.
+        NS = 3
+        streams = [torch.cuda.Stream() for _ in range(NS)]
         bufs = []
-        for j in range(2):
+        for j in range(NS):
             bufs.append((torch.from_numpy(batches[j % pool]).pin_memory(),
                          torch.empty(B, dtype=torch.uint64).pin_memory(),
                          torch.empty(B, dtype=torch.uint8).pin_memory(),
                          torch.empty(nbh, dtype=torch.uint8, device="cuda")))
-        if a.streams == 2:  # the same launch-shape caps as the device-resident pipelined loop
-            bt.bt_tree_set_corun(tree.handle, corun[0], corun[1])
-        for j in range(4):
-            h = bufs[j % 2]
-            bt.bt_search_batch_host(tree.handle, h[0], B, h[1], h[2], h[3], nbh, streams[j % 2])
+        for j in range(2 * NS):
+            h = bufs[j % NS]
+            bt.bt_search_batch_host(tree.handle, h[0], B, h[1], h[2], h[3], nbh, streams[j % NS])
         torch.cuda.synchronize()
         barrier(world)
         p0 = torch.cuda.Event(enable_timing=True)
         p1 = torch.cuda.Event(enable_timing=True)
-        fin = [torch.cuda.Event() for _ in range(2)]
+        fin = [torch.cuda.Event() for _ in range(NS)]
         p0.record(stream)
-        for j in range(2):
+        for j in range(NS):
             streams[j].wait_event(p0)
         for j in range(Ke):
-            h = bufs[j % 2]
-            bt.bt_search_batch_host(tree.handle, h[0], B, h[1], h[2], h[3], nbh, streams[j % 2])
-        for j in range(2):
+            h = bufs[j % NS]
+            bt.bt_search_batch_host(tree.handle, h[0], B, h[1], h[2], h[3], nbh, streams[j % NS])
+        for j in range(NS):
             fin[j].record(streams[j])
             stream.wait_event(fin[j])
         p1.record(stream)
         torch.cuda.synchronize()
         pipe_s = reduce_max(p0.elapsed_time(p1) / 1e3, world, device="cuda")
         pipelined = B * Ke * world / pipe_s
-        bt.bt_tree_set_corun(tree.handle, 0, 0)
         line["e2e"] = {"value": pipelined, "unit": UNIT, "h2d_bytes_per_step": B * kb,
                        "d2h_bytes_per_step": B * (vb + 1), "steps": Ke,
-                       "entry_point": "bt_search_batch_host (pinned host buffers), two streams alternating"
-                                      + (f", launch shapes capped at {corun[0]} descent / {corun[1]} partition "
-                                         "blocks per SM" if a.streams == 2 else ""),
+                       "entry_point": "bt_search_batch_host (pinned host buffers), three streams in turn",
                        "serial_value": serial, "serial_p50_us": 1e3 * sorted(tt)[len(tt) // 2],
                        "l2": "serial: flushed before every step; pipelined: not flushed (steps overlap; the "
                              "282 MB tree exceeds the 129 MB L2)"}
