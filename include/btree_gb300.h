@@ -220,8 +220,10 @@ bt_status bt_search_batch_ex(const bt_tree *tree, const void *d_queries, uint64_
  *   else f = c >> (bitlen(nsplit) - bits).
  * The batch is ordered by the coarse bucket f >> lb, lb = min(9, bits - 1),
  * and inside every coarse bucket of at most 1024 queries (the local sort's
- * tile; 256 for 32-byte keys) by f.  The order of queries with equal f, and inside larger coarse
- * buckets (a hot key) the order of queries with equal coarse buckets, is
+ * tile; 384 for 32-byte keys) by f.  The order of queries with equal f, and
+ * inside larger coarse buckets (a hot key, or automatic bits on batches
+ * from about 2^22 queries, 2^21 for 32-byte keys, where the 2^12 coarse
+ * buckets grow past the tile) the order of queries with equal coarse buckets, is
  * unspecified (it follows device atomics and may differ between calls).
  * One cooperative kernel (coarse counts, scatter, per-bucket local sort,
  * with two bounded grid barriers; see bt_check_timeouts) after one memset of

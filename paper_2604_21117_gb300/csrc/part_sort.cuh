@@ -61,7 +61,7 @@ constexpr int kSortGroups = kPartThreads / kSortThreads;
 template <typename K>
 __host__ __device__ constexpr int part_tile()
 {
-    return sizeof(K) > 8 ? 256 : 1024;
+    return sizeof(K) > 8 ? 384 : 1024;
 }
 
 // Per-search view of the tree's splitter table.
@@ -283,11 +283,24 @@ constexpr uint32_t kMaxPartBlocks = 1024;
 static __device__ unsigned int g_part_timeouts;
 
 // Queries of its slice a partition block keeps in shared memory between
-// counting and scattering (integer keys; 32-byte keys are read again).
+// counting and scattering: f and the query's rank in its bucket, and for
+// integer keys the key itself (32-byte keys are read again).
 template <typename K>
 __host__ __device__ constexpr uint32_t part_cache()
 {
-    return sizeof(K) > 8 ? 0u : 4096u;
+    return 4096u;
+}
+
+template <typename K>
+__host__ __device__ constexpr bool part_cache_keys()
+{
+    return sizeof(RawOf<K>) <= 8;
+}
+
+template <typename K>
+__host__ __device__ constexpr int part_cache_key_bytes()
+{
+    return part_cache_keys<K>() ? static_cast<int>(sizeof(RawOf<K>)) : 0;
 }
 
 // Dynamic shared memory of k_partition for nb coarse buckets: the block's
@@ -298,8 +311,8 @@ __host__ __device__ constexpr uint32_t part_cache()
 template <typename K>
 __host__ __device__ constexpr int part_area()
 {
-    return part_cache<K>() * static_cast<int>(sizeof(RawOf<K>) + 6) > kSortGroups * ((1 << kLocalBits) + 8) * 4
-               ? part_cache<K>() * static_cast<int>(sizeof(RawOf<K>) + 6)
+    return static_cast<int>(part_cache<K>()) * (part_cache_key_bytes<K>() + 6) > kSortGroups * ((1 << kLocalBits) + 8) * 4
+               ? static_cast<int>(part_cache<K>()) * (part_cache_key_bytes<K>() + 6)
                : kSortGroups * ((1 << kLocalBits) + 8) * 4;
 }
 
@@ -425,7 +438,7 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_partition(const RawOf<K> *_
     uint32_t *st = cnt + nb;
     unsigned char *area = reinterpret_cast<unsigned char *>(st + nb + 4);  // nb is a multiple of 4
     RawOf<K> *ck = reinterpret_cast<RawOf<K> *>(area);
-    uint32_t *cf = reinterpret_cast<uint32_t *>(ck + part_cache<K>());
+    uint32_t *cf = reinterpret_cast<uint32_t *>(area + part_cache<K>() * part_cache_key_bytes<K>());
     uint16_t *cr = reinterpret_cast<uint16_t *>(cf + part_cache<K>());
     part_load_tables(S, pn);
     for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x) cnt[j] = 0;
@@ -452,7 +465,7 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_partition(const RawOf<K> *_
                 if (cached) {
                     // the query's rank in its bucket within the slice: its
                     // place in the bucket's run, so the scatter needs no atomics
-                    ck[i] = key[u];
+                    if constexpr (part_cache_keys<K>()) ck[i] = key[u];
                     cf[i] = f;
                     cr[i] = static_cast<uint16_t>(atomicAdd(cnt + (f >> pn.lb), 1u));
                 } else {
@@ -501,7 +514,10 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_partition(const RawOf<K> *_
             const uint32_t i = i0 + u * blockDim.x;
             if (i < ns) {
                 if (cached) {
-                    key[u] = ck[i];
+                    if constexpr (part_cache_keys<K>())
+                        key[u] = ck[i];
+                    else
+                        key[u] = q[s0 + i];
                     f[u] = cf[i];
                 } else {
                     key[u] = q[s0 + i];

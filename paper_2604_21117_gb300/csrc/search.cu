@@ -102,9 +102,11 @@ static int bitlen(uint64_t x) { return x ? 64 - __builtin_clzll(x) : 0; }
 // Queries per batch from which the sort pays for itself by node reuse.
 constexpr uint64_t kAutoSortMinBatch = 16384;
 // Automatic bits: coarse buckets of 512 to 1023 queries on average (128 to
-// 255 for 32-byte keys; at least 2 buckets, at most 2^kMaxCoarseBits), each
-// ordered by kLocalBits more bits -- finer than one leaf per query at every
-// configured batch size.
+// 255 for 32-byte keys), each ordered by kLocalBits more bits -- finer than
+// one leaf per query at every configured batch size; at least 2 buckets and
+// at most 2^kMaxCoarseBits, so from 2^22 queries (2^21 for 32-byte keys) the
+// average bucket reaches the local sort's tile and larger buckets keep the
+// scatter's order.
 static int auto_part_bits(int key_bytes, uint64_t nq)
 {
     int cb = bitlen(nq) - (key_bytes > 8 ? 8 : 10);
