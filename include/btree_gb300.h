@@ -220,10 +220,10 @@ bt_status bt_search_batch_ex(const bt_tree *tree, const void *d_queries, uint64_
  *   else f = c >> (bitlen(nsplit) - bits).
  * The batch is ordered by the coarse bucket f >> lb, lb = min(9, bits - 1),
  * and inside every coarse bucket of at most 1024 queries (the local sort's
- * tile; 384 for 32-byte keys) by f.  The order of queries with equal f, and
- * inside larger coarse buckets (a hot key, or automatic bits on batches
- * from about 2^22 queries, 2^21 for 32-byte keys, where the 2^12 coarse
- * buckets grow past the tile) the order of queries with equal coarse buckets, is
+ * tile) by f.  The order of queries with equal f, and inside larger coarse
+ * buckets (a hot key, or automatic bits on batches from about 2^22 queries,
+ * where the 2^12 coarse buckets grow past the tile) the order of queries
+ * with equal coarse buckets, is
  * unspecified (it follows device atomics and may differ between calls).
  * One cooperative kernel (coarse counts, scatter, per-bucket local sort,
  * with two bounded grid barriers; see bt_check_timeouts) after one memset of
@@ -318,8 +318,9 @@ bt_status bt_search_batch_host(const bt_tree *tree, const void *h_queries, uint6
  * at zero), so calls whose work overlaps on the GPU -- on different streams,
  * or from different threads -- race and must be serialised by the caller.
  * Errors: as bt_search_batch, plus BT_ERR_ARG for nq > BT_NOALLOC_MAX_QUERIES
- * and BT_ERR_WORKSPACE when the batch's scratch exceeds the array (32-byte
- * keys: above about 43,000 queries).
+ * and BT_ERR_WORKSPACE when the batch's scratch would exceed the array (it
+ * does not at up to BT_NOALLOC_MAX_QUERIES queries: 65536 32-byte-key
+ * queries need 3.7 MB, integer keys 1.1 MB).
  */
 #define BT_NOALLOC_MAX_QUERIES 65536
 bt_status bt_search_batch_noalloc(const bt_tree *tree, const void *d_queries, uint64_t nq,

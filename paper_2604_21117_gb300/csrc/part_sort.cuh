@@ -25,9 +25,12 @@
 //             block's offset inside that bucket;
 //   scatter   bucket starts by a scan of the totals; every query goes to its
 //             block's run in its bucket, at its rank there (taken while
-//             counting), as one record (key, input position, digit);
+//             counting), as one record (key, input position, digit) -- for
+//             32-byte keys as an 8-byte (position, digit) pair;
 //   sort      groups of threads order the coarse buckets by digit, in
-//             place, several buckets per block at once.  Buckets of more
+//             place (32-byte keys: from the pairs into the records, each
+//             key read from the batch once), several buckets per block at
+//             once.  Buckets of more
 //             than part_tile<K>() queries (a hot key, or a coarse bucket far
 //             above its average size) keep the scatter's order.
 //
@@ -61,7 +64,16 @@ constexpr int kSortGroups = kPartThreads / kSortThreads;
 template <typename K>
 __host__ __device__ constexpr int part_tile()
 {
-    return sizeof(K) > 8 ? 384 : 1024;
+    return 1024;
+}
+
+// 32-byte keys scatter 8-byte (position, digit) pairs instead of 48-byte
+// records; the local sort writes each query's record once, in its final
+// place, reading the key from the batch.
+template <typename K>
+__host__ __device__ constexpr bool part_narrow()
+{
+    return sizeof(RawOf<K>) > 8;
 }
 
 // Per-search view of the tree's splitter table.
@@ -429,7 +441,7 @@ template <typename K>
 __global__ void __launch_bounds__(kPartThreads, 2) k_partition(const RawOf<K> *__restrict__ q, uint64_t nq,
                                                                PartNorm<K> pn, unsigned int *__restrict__ total,
                                                                uint32_t nb, PartRec<K> *__restrict__ rec,
-                                                               uint32_t polls)
+                                                               uint2 *__restrict__ pairs, uint32_t polls)
 {
     __shared__ PartSmem<K> S;
     extern __shared__ __align__(16) unsigned char dsm[];
@@ -516,7 +528,7 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_partition(const RawOf<K> *_
                 if (cached) {
                     if constexpr (part_cache_keys<K>())
                         key[u] = ck[i];
-                    else
+                    else if constexpr (!part_narrow<K>())
                         key[u] = q[s0 + i];
                     f[u] = cf[i];
                 } else {
@@ -531,16 +543,20 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_partition(const RawOf<K> *_
                 if (!cached) f[u] = part_bucket(S, pn, KeyOps<K>::from_raw(key[u]));
                 const uint32_t pos = cached ? cnt[f[u] >> pn.lb] + cr[i] : atomicAdd(cnt + (f[u] >> pn.lb), 1u);
                 if (pos < nq) {  // always true when the counts agree; keeps a stray write in bounds
-                    PartRec<K> r;
-                    r.key = key[u];
-                    r.idx = static_cast<uint32_t>(s0 + i);
-                    r.digit = f[u] & dmask;
-                    rec[pos] = r;
+                    if constexpr (part_narrow<K>()) {
+                        pairs[pos] = make_uint2(static_cast<uint32_t>(s0 + i), f[u] & dmask);
+                    } else {
+                        PartRec<K> r;
+                        r.key = key[u];
+                        r.idx = static_cast<uint32_t>(s0 + i);
+                        r.digit = f[u] & dmask;
+                        rec[pos] = r;
+                    }
                 }
             }
         }
     }
-    if (pn.lb == 0) return;
+    if (pn.lb == 0 && !part_narrow<K>()) return;
     if (!part_grid_sync(total + nb + 1, polls, &S.last)) {
         if (threadIdx.x == 0) atomicAdd(&g_part_timeouts, 1u);
         return;
@@ -559,6 +575,58 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_partition(const RawOf<K> *_
     uint32_t *gb = reinterpret_cast<uint32_t *>(area) + grp * ((1 << kLocalBits) + 8);
     uint32_t *gtmp = gb + (1 << kLocalBits);  // per-warp partial sums of the group's scan
     constexpr int EL = part_tile<K>() / kSortThreads;
+    if constexpr (part_narrow<K>()) {
+        // every bucket's pairs become records: sorted by digit when the
+        // bucket fits the tile, else in scatter order
+        for (uint32_t b = blockIdx.x * kSortGroups + grp; b < nb; b += gridDim.x * kSortGroups) {
+            const uint32_t bs = st[b];
+            const uint32_t n = st[b + 1] - bs;
+            if (n == 0) continue;
+            if (n > static_cast<uint32_t>(part_tile<K>()) || pn.lb == 0) {
+                for (uint32_t i = gtid; i < n; i += kSortThreads) {
+                    const uint2 pr = __ldcg(pairs + bs + i);
+                    PartRec<K> r;
+                    r.key = q[pr.x];
+                    r.idx = pr.x;
+                    r.digit = pr.y;
+                    rec[bs + i] = r;
+                }
+                continue;
+            }
+            for (uint32_t j = gtid; j < nscan; j += kSortThreads) gb[j] = 0;
+            part_group_sync(grp);
+            uint2 pr[EL];
+            uint32_t rk[EL];
+#pragma unroll
+            for (int e = 0; e < EL; ++e) {
+                const uint32_t i = gtid + e * kSortThreads;
+                if (i < n) pr[e] = __ldcg(pairs + bs + i);
+            }
+#pragma unroll
+            for (int e = 0; e < EL; ++e) {
+                const uint32_t i = gtid + e * kSortThreads;
+                if (i < n) rk[e] = atomicAdd(gb + (pr[e].y & (nd - 1u)), 1u);
+            }
+            part_group_sync(grp);
+            part_group_scan(gb, nscan, gtmp, grp, gtid);
+#pragma unroll
+            for (int e = 0; e < EL; ++e) {
+                const uint32_t i = gtid + e * kSortThreads;
+                if (i < n) {
+                    const uint32_t p = gb[pr[e].y & (nd - 1u)] + rk[e];
+                    if (p < n) {  // always true; keeps a stray write inside the bucket
+                        PartRec<K> r;
+                        r.key = q[pr[e].x];
+                        r.idx = pr[e].x;
+                        r.digit = pr[e].y;
+                        rec[bs + p] = r;
+                    }
+                }
+            }
+            part_group_sync(grp);
+        }
+        return;
+    }
     for (uint32_t b = blockIdx.x * kSortGroups + grp; b < nb; b += gridDim.x * kSortGroups) {
         const uint32_t bs = st[b];
         const uint32_t n = st[b + 1] - bs;

@@ -71,7 +71,7 @@ __global__ void k_fill_miss(V *__restrict__ out_v, uint8_t *__restrict__ out_f, 
 static inline uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
 
 struct WsLayout {
-    uint64_t rec, counts, total;
+    uint64_t rec, pairs, counts, total;
 };
 
 // Coarse-bucket totals of the partition and its two grid-barrier counters:
@@ -82,8 +82,9 @@ constexpr uint64_t kPartCountWords = (1ull << kMaxCoarseBits) + 4;
 constexpr uint64_t kPartPerBlock = 2048;
 
 // Workspace: the partitioned batch (one record per query: key, input
-// position, local digit) and the partition's bucket totals and barrier
-// counters.
+// position, local digit), for 32-byte keys the scattered (position, digit)
+// pairs the records are made from, and the partition's bucket totals and
+// barrier counters.
 static WsLayout ws_layout(int kb, uint64_t nq)
 {
     WsLayout w;
@@ -91,6 +92,8 @@ static WsLayout ws_layout(int kb, uint64_t nq)
     const uint64_t rb = kb > 8 ? sizeof(PartRec<Key32>) : sizeof(PartRec<uint64_t>);
     w.rec = o;
     o = align256(o + nq * rb);
+    w.pairs = o;
+    if (kb > 8) o = align256(o + nq * 8);
     w.counts = o;
     o = align256(o + kPartCountWords * 4);
     w.total = nq ? o : 0;
@@ -101,15 +104,15 @@ static int bitlen(uint64_t x) { return x ? 64 - __builtin_clzll(x) : 0; }
 
 // Queries per batch from which the sort pays for itself by node reuse.
 constexpr uint64_t kAutoSortMinBatch = 16384;
-// Automatic bits: coarse buckets of 512 to 1023 queries on average (128 to
-// 255 for 32-byte keys), each ordered by kLocalBits more bits -- finer than
-// one leaf per query at every configured batch size; at least 2 buckets and
-// at most 2^kMaxCoarseBits, so from 2^22 queries (2^21 for 32-byte keys) the
-// average bucket reaches the local sort's tile and larger buckets keep the
-// scatter's order.
+// Automatic bits: coarse buckets of 512 to 1023 queries on average, each
+// ordered by kLocalBits more bits -- finer than one leaf per query at every
+// configured batch size; at least 2 buckets and at most 2^kMaxCoarseBits,
+// so from 2^22 queries the average bucket reaches the local sort's tile and
+// larger buckets keep the scatter's order.
 static int auto_part_bits(int key_bytes, uint64_t nq)
 {
-    int cb = bitlen(nq) - (key_bytes > 8 ? 8 : 10);
+    (void)key_bytes;
+    int cb = bitlen(nq) - 10;
     cb = cb < 1 ? 1 : (cb > kMaxCoarseBits ? kMaxCoarseBits : cb);
     return cb + kLocalBits;
 }
@@ -196,6 +199,7 @@ static cudaError_t part_sort(const DevTree &t, const RawOf<K> *q, uint64_t nq, c
     pn.wmin = t.split_wmin;
     unsigned int *total = reinterpret_cast<unsigned int *>(ws + w.counts);
     PartRec<K> *rec = reinterpret_cast<PartRec<K> *>(ws + w.rec);
+    uint2 *pairs = part_narrow<K>() ? reinterpret_cast<uint2 *>(ws + w.pairs) : nullptr;
     cudaError_t e = cudaMemsetAsync(total, 0, (static_cast<uint64_t>(pp.nb) + 4) * 4, s);
     if (e != cudaSuccess) return e;
     const void *kern = reinterpret_cast<const void *>(k_partition<K>);
@@ -214,7 +218,7 @@ static cudaError_t part_sort(const DevTree &t, const RawOf<K> *q, uint64_t nq, c
     if (g > cap) g = cap;
     if (g > kMaxPartBlocks) g = kMaxPartBlocks;
     uint32_t nb = pp.nb, polls = first_wait_polls();
-    void *args[] = {const_cast<RawOf<K> **>(&q), &nq, &pn, &total, &nb, &rec, &polls};
+    void *args[] = {const_cast<RawOf<K> **>(&q), &nq, &pn, &total, &nb, &rec, &pairs, &polls};
     return cudaLaunchCooperativeKernel(kern, dim3(static_cast<unsigned>(g)), dim3(kPartThreads), args,
                                        static_cast<size_t>(dyn), s);
 }

@@ -18,7 +18,7 @@ LOCAL_BITS = 9
 
 def tile_for(key_bytes: int) -> int:
     """Largest coarse bucket the local sort orders."""
-    return 384 if key_bytes > 8 else 1024
+    return 1024
 
 
 def part_plan(bits: int, nsplit: int):
