@@ -46,6 +46,27 @@ def test_noalloc_matches_workspace_entry_point_on_two_calls(bt):
     tree.close()
 
 
+def test_noalloc_32_byte_keys_at_its_limit_against_the_oracle(bt):
+    """The largest no-allocation batch of the paper's 32-byte keys (the
+    partition's pairs and records fit the scratch), every result against the
+    byte-key oracle."""
+    import torch
+    from oracle.bytes_keys import OracleBytesTree
+    keys = W.byte_keys(200_000, 32, seed=35)
+    vals = W.rank_values(keys.shape[0], 64)
+    tree = bt.BTree(keys, vals, 16)
+    o = OracleBytesTree(keys, vals, 16)
+    nq = bt.BT_NOALLOC_MAX_QUERIES
+    qh = W.make_byte_queries(keys, nq, 0.9, seed=36)
+    v, f = tree.alloc_outputs(nq)
+    bt.bt_search_batch_noalloc(tree.handle, torch.from_numpy(qh).cuda(), nq, v, f)
+    torch.cuda.synchronize()
+    ov, of, _, _ = o.search(qh)
+    assert np.array_equal(v.cpu().numpy(), ov) and np.array_equal(f.cpu().numpy(), of)
+    o.close()
+    tree.close()
+
+
 def test_noalloc_rejects_batches_above_its_limit(bt):
     import torch
     keys = W.uniform_keys(1000, 64, seed=34)
