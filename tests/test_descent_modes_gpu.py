@@ -154,3 +154,54 @@ def test_two_streams_with_corun_caps(bt, caps):
         assert np.array_equal(v, want[qi][0]) and np.array_equal(f, want[qi][1])
     bt.bt_tree_set_corun(tree.handle, 0, 0)
     tree.close()
+
+
+@pytest.mark.parametrize("kind", ["bytes32", "learned"])
+def test_two_streams_with_corun_caps_other_paths(bt, kind):
+    """The same two-stream pattern over 32-byte keys and over the learned
+    search: results equal the oracle's."""
+    import torch
+    B = 50_003
+    if kind == "bytes32":
+        from oracle.bytes_keys import OracleBytesTree
+        keys = W.byte_keys(100_000, 32, seed=141)
+        vals = W.rank_values(keys.shape[0], 64)
+        tree = bt.BTree(keys, vals, 16)
+        o = OracleBytesTree(keys, vals, 16)
+        qs = [W.make_byte_queries(keys, B, 0.9, seed=142 + i) for i in range(2)]
+        mdl = None
+    else:
+        keys = W.lognormal_mixture_keys(300_000, seed=143)
+        vals = W.rank_values(keys.size, 64)
+        tree = bt.BTree(keys, vals, 32)
+        o = OracleTree(keys, vals, 32)
+        qs = [W.make_queries(keys, B, 0.9, seed=144 + i, width_bits=64) for i in range(2)]
+        mdl = bt.bt_model_train(tree.handle, bt.BT_MODEL_PL, segments=256)
+    bt.bt_tree_set_corun(tree.handle, 0, 1)
+    want = [o.search(q)[:2] for q in qs]
+    nb = tree.workspace_bytes(B)
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    outs = []
+    for i in range(2):
+        ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        v, f = tree.alloc_outputs(B)
+        dq = torch.from_numpy(qs[i]).cuda()
+        torch.cuda.synchronize()
+        outs.append((ws, v, f, dq))
+    for rep in range(3):
+        for i in range(2):
+            ws, v, f, dq = outs[i]
+            if mdl is None:
+                bt.bt_search_batch(tree.handle, dq, B, v, f, ws, nb, streams[i])
+            else:
+                bt.bt_learned_search_batch(tree.handle, mdl, dq, B, v, f, ws, nb, streams[i])
+    torch.cuda.synchronize()
+    bt.bt_check_timeouts()
+    for i in range(2):
+        _, v, f, _ = outs[i]
+        assert np.array_equal(v.cpu().numpy().astype(np.uint64), want[i][0])
+        assert np.array_equal(f.cpu().numpy(), want[i][1])
+    if mdl is not None:
+        bt.bt_model_free(mdl)
+    o.close()
+    tree.close()
