@@ -568,7 +568,10 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_partition(const RawOf<K> *_
     // of kSortThreads, each ordering one coarse bucket of at most part_tile
     // records at a time by digit (records in registers, ranks among equal
     // digits from shared-memory atomics, a scan of the digit counts; the
-    // group synchronises on its own named barrier).
+    // group synchronises on its own named barrier).  Buckets go to the
+    // groups group-major (bucket b to group b / gridDim.x of block
+    // b % gridDim.x, then round after round), so that the buckets beyond the
+    // first round spread over all blocks, and so over all SMs.
     const uint32_t nd = 1u << pn.lb;
     const uint32_t nscan = nd < 4 ? 4 : nd;  // the scan works on groups of 4 counters
     const uint32_t grp = threadIdx.x / kSortThreads, gtid = threadIdx.x % kSortThreads;
@@ -578,7 +581,7 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_partition(const RawOf<K> *_
     if constexpr (part_narrow<K>()) {
         // every bucket's pairs become records: sorted by digit when the
         // bucket fits the tile, else in scatter order
-        for (uint32_t b = blockIdx.x * kSortGroups + grp; b < nb; b += gridDim.x * kSortGroups) {
+        for (uint32_t b = grp * gridDim.x + blockIdx.x; b < nb; b += gridDim.x * kSortGroups) {
             const uint32_t bs = st[b];
             const uint32_t n = st[b + 1] - bs;
             if (n == 0) continue;
@@ -627,7 +630,7 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_partition(const RawOf<K> *_
         }
         return;
     }
-    for (uint32_t b = blockIdx.x * kSortGroups + grp; b < nb; b += gridDim.x * kSortGroups) {
+    for (uint32_t b = grp * gridDim.x + blockIdx.x; b < nb; b += gridDim.x * kSortGroups) {
         const uint32_t bs = st[b];
         const uint32_t n = st[b + 1] - bs;
         if (n <= 1 || n > static_cast<uint32_t>(part_tile<K>())) continue;  // the same for the whole group
