@@ -92,6 +92,7 @@ def parse_args(argv=None):
     p.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain leg")
     p.add_argument("--no-batching", action="store_true", help="skip the multi-tree batching leg")
     p.add_argument("--no-serving", action="store_true", help="skip the serving leg")
+    p.add_argument("--no-range", action="store_true", help="skip the range-partitioned leg")
     p.add_argument("--no-paper-keys", action="store_true", help="skip the 32-byte-key leg")
     p.add_argument("--no-sweeps", action="store_true", help="skip the batch-size and tree-size sweeps")
     return p.parse_args(argv)
@@ -803,6 +804,45 @@ def batching_leg(a, bt, stream, nbatches: int = 10_000):
             "bit_exact_vs_single_tree_path": ok}
 
 
+# ------------------------------------------------------- range-split leg
+
+def range_leg(a, bt, keys, vals, dq, ref, stream, steps: int = 30):
+    """Range-partitioned trees on one GPU (bt_range_build / bt_range_search):
+    the default tree's keys split into P contiguous key ranges, each its own
+    tree; a batch is routed to its parts, each part searched, the results
+    returned in input order.  Lookups/s per P against the single tree, and
+    the results of one batch against the single tree's."""
+    import torch
+    B = a.batch
+    out = {"workload": f"{a.keys} uniform uint64 keys split into P key ranges, fanout {a.fanout}, "
+                       f"batches of {B} queries (the default workload's)", "parts": {}}
+    for P in (1, 2, 4, 8):
+        r = bt.bt_range_build(keys, vals, a.fanout, P, stream=stream)
+        nb = bt.bt_range_workspace_bytes(r, B)
+        ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        v = torch.empty(B, dtype=torch.uint64, device="cuda")
+        f = torch.empty(B, dtype=torch.uint8, device="cuda")
+        for i in range(3):
+            bt.bt_range_search(r, dq[i % len(dq)], B, v, f, ws, nb, stream)
+        torch.cuda.synchronize()
+        ev = []
+        for i in range(steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            bt.bt_range_search(r, dq[i % len(dq)], B, v, f, ws, nb, stream)
+            e1.record(stream)
+            ev.append((e0, e1))
+        torch.cuda.synchronize()
+        us = sorted(1e3 * x.elapsed_time(y) for x, y in ev)
+        bt.bt_range_search(r, dq[0], B, v, f, ws, nb, stream)
+        torch.cuda.synchronize()
+        same = bool(np.array_equal(v.cpu().numpy(), ref[0]) and np.array_equal(f.cpu().numpy(), ref[1]))
+        out["parts"][str(P)] = {"lookups_per_s": B / (statistics.fmean(us) / 1e6), "p50_us": us[len(us) // 2],
+                                "bit_exact_vs_single_tree": same}
+        bt.bt_range_free(r)
+    return out
+
+
 # ------------------------------------------------------- serving leg
 
 def serving_leg(a, bt, rates=(1e6, 5e6, 20e6, 50e6, 100e6), seconds: float = 0.25):
@@ -1219,6 +1259,12 @@ def run_ours(a):
         line["batching"] = batching_leg(a, bt, stream)
     if not a.no_extras and not a.no_serving:
         line["serving"] = serving_leg(a, bt)
+    if not a.no_extras and not a.no_range:
+        # the single tree's results of batch 0, for the range leg's check
+        bt.bt_search_batch(tree.handle, dq[0], B, out_v, out_f, ws, nb, stream)
+        torch.cuda.synchronize()
+        ref0 = (out_v.cpu().numpy().copy(), out_f.cpu().numpy().copy())
+        line["range_split"] = range_leg(a, bt, keys, vals, dq, ref0, stream)
 
     sampler.stop()
     line["clocks"] = sampler.summary()
