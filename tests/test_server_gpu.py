@@ -170,3 +170,23 @@ def test_many_trees_and_32_bit_keys(bt):
         ov, of, _, _ = trees[tr][3].search(q)
         assert np.array_equal(v.astype(np.uint64), ov) and np.array_equal(f, of)
     bt.bt_server_destroy(srv)
+
+
+def test_rings_wrap_many_times(bt, two_trees):
+    """A ring of 3 * max_batch lookups per tree and one slot: thousands of
+    requests wrap the rings again and again (requests never straddle the end:
+    the space before it is skipped), and a tree's stretch in a batch splits
+    into two work-list entries where it wraps; every request equals the
+    oracle."""
+    srv = bt.bt_server_create([t[2] for t in two_trees], None, slots=1, max_batch=64, deadline_us=1.0)
+    keys, offs, sizes, tids, t = _trace(two_trees, 3000, seed=89, rate=2e6)
+    vals = np.zeros(keys.size, np.uint64)
+    found = np.full(keys.size, 9, np.uint8)
+    bt.bt_server_run_trace(srv, t, tids, sizes, offs, keys, vals, found)
+    st = bt.bt_server_get_stats(srv)
+    assert st.completed == 3000 and st.lookups == keys.size and st.batches >= keys.size // 64
+    for r in range(3000):
+        o, c, tr = int(offs[r]), int(sizes[r]), int(tids[r])
+        ov, of, _, _ = two_trees[tr][3].search(keys[o:o + c])
+        assert np.array_equal(vals[o:o + c], ov) and np.array_equal(found[o:o + c], of), r
+    bt.bt_server_destroy(srv)
