@@ -573,10 +573,11 @@ def paper_keys_leg(a, bt, flush, stream, peak):
                "correct": bool(np.array_equal(v.cpu().numpy(), want_v) and
                                np.array_equal(f.cpu().numpy(), hit.astype(np.uint8)))}
         if B > 4096:
-            # the descent alone on the partitioned batch, against its algorithmic bytes
+            # the descent alone on the batch partitioned on log2 B bits, against its
+            # algorithmic bytes
             sq = torch.empty_like(q)
             si = torch.empty(B, dtype=torch.int32, device="cuda")
-            bt.bt_sort_batch(tree.handle, q, B, -1, sq, si, ws, nb, stream)
+            bt.bt_sort_batch(tree.handle, q, B, B.bit_length() - 1, sq, si, ws, nb, stream)
             dfn = lambda: bt.bt_descend_sorted(tree.handle, sq, si, B, v, f, None, stream)
             dus = _time_calls(dfn, steps, flush, stream)
             counts, sect = rank_touched(n, tree.level_nodes, m, rank, hit, 8)

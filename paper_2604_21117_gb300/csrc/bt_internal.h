@@ -44,6 +44,12 @@ struct DevTree {
     // previous batch's descent (bt_tree_set_corun).
     int corun_descent_bps;
     int corun_partition_bps;
+    // 1 when the tree's device image is larger than a quarter of the
+    // device's L2: only then does the automatic choice partition large
+    // batches (a smaller tree's leaves stay in the L2 between batches, and
+    // the unsorted descent reads them from there faster than the partition
+    // takes).
+    int sort_pays;
     // Splitters of the batch partition: the largest keys of nsplit evenly
     // spaced leaves, and nsplit + 1 reciprocal widths of the key segments
     // they bound (part_sort.cuh).

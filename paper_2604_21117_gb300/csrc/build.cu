@@ -349,6 +349,12 @@ extern "C" bt_status bt_build(const void *h_keys, const void *h_vals, uint64_t n
     d.inner_stage = 2;  // staged for partitioned batches, through L1 otherwise
     d.corun_descent_bps = 0;
     d.corun_partition_bps = 0;
+    {
+        int dev = 0, l2 = 0;
+        const bool known = cudaGetDevice(&dev) == cudaSuccess &&
+                           cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) == cudaSuccess && l2 > 0;
+        d.sort_pays = (!known || off > static_cast<uint64_t>(l2) / 4) ? 1 : 0;
+    }
     set_pin_levels(d, t->info, 16384);
 
     // Shape arithmetic: children (or keys, for leaves) per node.

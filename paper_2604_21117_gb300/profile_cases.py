@@ -2,6 +2,7 @@
 
     python -m paper_2604_21117_gb300.profile_cases forest [warps pin_budget lane_queries staging]
     python -m paper_2604_21117_gb300.profile_cases keys32 [sorted|full]
+    python -m paper_2604_21117_gb300.profile_cases crossover
 
 forest: the multi-tree batching workload -- trees of 10^3, 10^5, 10^6 and
 2*10^7 uniform uint64 keys at fanout 32, a work list of 10,000 batches whose
@@ -12,7 +13,13 @@ through L1).
 
 keys32: the paper's own tree (2^20 distinct 32-byte keys, 8-byte values,
 fanout 16) and a batch of 2^20 uniform queries at 90% hits: six descents of
-the partitioned batch (sorted) or six whole searches (full).
+the batch partitioned on 20 bits (sorted) or six whole searches (full).
+
+crossover: whole searches (bt_search_batch_ex) with no partition and with
+a partition on log2 B bits, batches B of 2^16 to 2^20 queries at 90% hits,
+over three trees that the L2 could hold -- 2^20 32-byte keys at fanout 16,
+and 10^6 and 4 * 10^6 uint64 keys at fanout 32 -- each with the L2 left warm
+and with a 256 MB write before every call; medians of 40 calls.
 
 Each prints its CUDA-event times; the inputs come from workloads.py with
 fixed seeds.
@@ -94,7 +101,7 @@ def keys32(mode: str = "sorted") -> None:
     s = torch.cuda.current_stream()
     sq = torch.empty_like(q)
     si = torch.empty(B, dtype=torch.int32, device="cuda")
-    bt.bt_sort_batch(tree.handle, q, B, -1, sq, si, ws, nb, s)
+    bt.bt_sort_batch(tree.handle, q, B, 20, sq, si, ws, nb, s)
     for it in range(6):
         e0, e1 = _events()
         e0.record(s)
@@ -108,15 +115,69 @@ def keys32(mode: str = "sorted") -> None:
     tree.close()
 
 
+def crossover(steps: int = 40) -> None:
+    import statistics
+    import torch
+    from . import build_lib
+    build_lib.build()
+    from . import btree as bt
+    from . import workloads as W
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.current_stream()
+
+    def median_us(fn, flushing):
+        for _ in range(3):
+            fn()
+        ev = []
+        for i in range(steps):
+            if flushing:
+                flush.fill_(i & 255)
+            e0, e1 = _events()
+            e0.record(s)
+            fn()
+            e1.record(s)
+            ev.append((e0, e1))
+        torch.cuda.synchronize()
+        return statistics.median(1000 * a.elapsed_time(b) for a, b in ev)
+
+    kb = W.byte_keys(1 << 20, 32, seed=W.SEED_BASE + 8)
+    k6 = W.uniform_keys(1_000_000, 64, seed=W.SEED_BASE + 3)
+    k7 = W.uniform_keys(4_000_000, 64, seed=W.SEED_BASE + 4)
+    cases = [
+        ("2^20 32-byte keys, m=16", bt.BTree(kb, W.rank_values(kb.shape[0], 64), 16),
+         lambda B: W.make_byte_queries(kb, B, 0.9, seed=W.SEED_BASE + 9 + B)),
+        ("10^6 uint64 keys, m=32", bt.BTree(k6, W.rank_values(k6.size, 64), 32),
+         lambda B: W.make_queries(k6, B, 0.9, seed=B + 5, width_bits=64)),
+        ("4*10^6 uint64 keys, m=32", bt.BTree(k7, W.rank_values(k7.size, 64), 32),
+         lambda B: W.make_queries(k7, B, 0.9, seed=B + 6, width_bits=64)),
+    ]
+    for name, tree, make in cases:
+        mb = int(bt.bt_tree_info(tree.handle).device_bytes) / 1e6
+        for B in (1 << 16, 1 << 18, 1 << 19, 1 << 20):
+            q = torch.from_numpy(make(B)).cuda()
+            nb = tree.workspace_bytes(B)
+            ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+            v, f = tree.alloc_outputs(B)
+            cols = []
+            for flushing in (False, True):
+                for sb in (0, B.bit_length() - 1):
+                    fn = lambda sb=sb: bt.bt_search_batch_ex(tree.handle, q, B, v, f, ws, nb, sb, None, s)
+                    cols.append(f"{'flushed' if flushing else 'warm'} bits={sb}: {median_us(fn, flushing):.1f} us")
+            print(f"{name} ({mb:.0f} MB), {B} queries: " + " | ".join(cols), flush=True)
+        tree.close()
+
+
 def main(argv=None) -> int:
     argv = sys.argv[1:] if argv is None else argv
-    if not argv or argv[0] not in ("forest", "keys32"):
+    if not argv or argv[0] not in ("forest", "keys32", "crossover"):
         print(__doc__)
         return 2
     if argv[0] == "forest":
         forest(*(int(x) for x in argv[1:5]))
-    else:
+    elif argv[0] == "keys32":
         keys32(*argv[1:2])
+    else:
+        crossover()
     return 0
 
 

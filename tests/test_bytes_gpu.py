@@ -151,7 +151,7 @@ def test_partition_orders_by_splitter_segment(bt):
     sq = torch.empty_like(dq)
     si = torch.empty(q.shape[0], dtype=torch.int32, device="cuda")
     ws, nb = tree.alloc_workspace(q.shape[0])
-    bt.bt_sort_batch(tree.handle, dq, q.shape[0], -1, sq, si, ws, nb)
+    bt.bt_sort_batch(tree.handle, dq, q.shape[0], 16, sq, si, ws, nb)
     hsq, hsi = sq.cpu().numpy(), si.cpu().numpy().view(np.uint32)
     assert np.array_equal(np.sort(hsi), np.arange(q.shape[0], dtype=np.uint32))
     assert np.array_equal(hsq, q[hsi])
@@ -162,7 +162,7 @@ def test_partition_orders_by_splitter_segment(bt):
     sp_words = img[o: o + ns * 32].view(np.uint64).reshape(ns, 4)
     sp = [sp_words[j].astype(">u8").tobytes() for j in range(ns)]
     c = np.array([bisect.bisect_left(sp, bytes(r)) for r in hsq])
-    sortcheck.check_order(c, bt.bt_sort_bits(tree.handle, q.shape[0], -1), ns, sortcheck.tile_for(32))
+    sortcheck.check_order(c, bt.bt_sort_bits(tree.handle, q.shape[0], 16), ns, sortcheck.tile_for(32))
     v, f = tree.alloc_outputs(q.shape[0])
     bt.bt_descend_sorted(tree.handle, sq, si, q.shape[0], v, f)
     ov, of, _, _ = OracleBytesTree(keys, vals, 32).search(q)

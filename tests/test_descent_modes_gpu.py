@@ -44,8 +44,9 @@ def _same(tree, o, q, sort_bits=-1):
 @pytest.mark.parametrize("m", [8, 16, 32, 64])
 @pytest.mark.parametrize("kw,vw", [(32, 32), (64, 64), (64, 32)])
 def test_pipelined_options(bt, inner, ballot, m, kw, vw):
-    """Every fanout and width; sorted (auto, forced) and unsorted batches;
-    a ragged size, so the last chunk has tail lanes."""
+    """Every fanout and width; sorted (12 bits) and unsorted batches (the
+    automatic choice on this small tree, and forced); a ragged size,
+    so the last chunk has tail lanes."""
     keys = W.uniform_keys(90_000 + m, kw, seed=500 + m + kw)
     vals = W.rank_values(keys.size, vw)
     tree = bt.BTree(keys, vals, m)
@@ -68,6 +69,8 @@ def test_staging_modes_and_sizes(bt, staging, nq):
     o = OracleTree(keys, vals, 32)
     q = W.make_queries(keys, nq, 0.9, seed=611 + nq, width_bits=64)
     _same(tree, o, q)
+    if nq >= 1000:
+        _same(tree, o, q, 16)
     bt.bt_check_timeouts()
 
 

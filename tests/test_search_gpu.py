@@ -223,6 +223,8 @@ def test_full_size_2p24_keys_fanout32(bt, zipf):
     o = OracleTree(keys, vals, 32)
     for b in (1, 16, 64, 256, 1024, 1 << 20):
         q = W.make_queries(keys, b, 0.9, seed=W.SEED_BASE + 1000 + b, width_bits=64, zipf_s=zipf)
+        # the tree's image exceeds the L2: the automatic choice partitions 2^20 queries only
+        assert (bt.bt_sort_bits(tree.handle, b, -1) > 9) == (b == 1 << 20)
         _check(tree, o, q, -1)
         if b == 1 << 20:
             _check(tree, o, q, 0)
@@ -264,8 +266,8 @@ def _check_sort_contract(bt, tree, keys, q, hsq, hsi, sb):
         return
     if sb > 0:
         assert bits == min(sb, 21)
-    if sb < 0:
-        assert bits == 0 if nq < 16384 else bits > 9
+    if sb < 0:  # automatic: only for large batches on trees larger than a quarter of the L2
+        assert nq >= 786432 and bits > 9
     k = hsq.astype(np.uint64)
     c = np.searchsorted(sp, k, side="left")
     lo = np.concatenate([[int(keys[0])], sp.astype(object)]) if nsplit else np.array([int(keys[0])], object)
@@ -302,7 +304,8 @@ def test_split_sort_then_descend(bt, kw, sb):
 def test_sort_contract_sizes_and_skew(bt, dist, nq):
     """The partition on skewed input (a hot key's bucket holds most of the
     batch), skewed keys (splitter segments follow the key distribution) and
-    sizes around the auto-partition threshold."""
+    sizes from 1 to 2^20; the tree is small (5 MB), so the automatic choice
+    is no partition at every size."""
     keys = W.lognormal_mixture_keys(300_000, seed=20) if dist == "lognormal" else W.uniform_keys(300_000, 64, seed=20)
     tree = bt.BTree(keys, W.rank_values(keys.size, 64), 32)
     if dist == "same":

@@ -29,8 +29,8 @@ def test_noalloc_matches_workspace_entry_point_on_two_calls(bt):
     keys = W.uniform_keys(300_000, 64, seed=31)
     vals = W.rank_values(keys.size, 64)
     tree = bt.BTree(keys, vals, 32)
-    # the largest batch (sorted path) then a ragged one: the second call
-    # runs on scratch that still holds the first call's contents
+    # the largest batch then a ragged one: the second call runs on scratch
+    # that still holds the first call's contents
     for nq, seed in ((bt.BT_NOALLOC_MAX_QUERIES, 32), (40_001, 33)):
         q = torch.from_numpy(W.make_queries(keys, nq, 0.9, seed=seed, width_bits=64, zipf_s=1.1)).cuda()
         v_ref, f_ref = tree.alloc_outputs(nq)
@@ -48,8 +48,8 @@ def test_noalloc_matches_workspace_entry_point_on_two_calls(bt):
 
 def test_noalloc_32_byte_keys_at_its_limit_against_the_oracle(bt):
     """The largest no-allocation batch of the paper's 32-byte keys (the
-    partition's pairs and records fit the scratch), every result against the
-    byte-key oracle."""
+    workspace it asks for, sized for a partition's pairs and records, fits
+    the scratch), every result against the byte-key oracle."""
     import torch
     from oracle.bytes_keys import OracleBytesTree
     keys = W.byte_keys(200_000, 32, seed=35)
