@@ -3,6 +3,7 @@
     python -m paper_2604_21117_gb300.profile_cases forest [warps pin_budget lane_queries staging]
     python -m paper_2604_21117_gb300.profile_cases keys32 [sorted|full]
     python -m paper_2604_21117_gb300.profile_cases crossover
+    python -m paper_2604_21117_gb300.profile_cases shapes
 
 forest: the multi-tree batching workload -- trees of 10^3, 10^5, 10^6 and
 2*10^7 uniform uint64 keys at fanout 32, a work list of 10,000 batches whose
@@ -20,6 +21,11 @@ a partition on log2 B bits, batches B of 2^16 to 2^20 queries at 90% hits,
 over three trees that the L2 could hold -- 2^20 32-byte keys at fanout 16,
 and 10^6 and 4 * 10^6 uint64 keys at fanout 32 -- each with the L2 left warm
 and with a 256 MB write before every call; medians of 40 calls.
+
+shapes: the descent of 2^20 queries partitioned on 20 bits over 2^24 uniform
+uint64 keys at fanout 32 (four batches in turn), at 4, 8 and 16 warps per
+block and 1 to 8 resident blocks per SM (bt_tree_set_corun; "max" = as many
+as fit); medians of 60 launches.
 
 Each prints its CUDA-event times; the inputs come from workloads.py with
 fixed seeds.
@@ -167,17 +173,61 @@ def crossover(steps: int = 40) -> None:
         tree.close()
 
 
+def shapes(steps: int = 60) -> None:
+    import statistics
+    import torch
+    from . import build_lib
+    build_lib.build()
+    from . import btree as bt
+    from . import workloads as W
+    n, B = 1 << 24, 1 << 20
+    keys = W.uniform_keys(n, 64, seed=W.SEED_BASE + 2)
+    tree = bt.BTree(keys, W.rank_values(n, 64), 32)
+    nb = tree.workspace_bytes(B)
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    v, f = tree.alloc_outputs(B)
+    s = torch.cuda.current_stream()
+    batches = []
+    for i in range(4):
+        q = torch.from_numpy(W.make_queries(keys, B, 0.9, seed=W.SEED_BASE + 2 + 1000 * (i + 1), width_bits=64)).cuda()
+        sq = torch.empty_like(q)
+        si = torch.empty(B, dtype=torch.int32, device="cuda")
+        bt.bt_sort_batch(tree.handle, q, B, 20, sq, si, ws, nb, s)
+        batches.append((sq, si))
+    for warps in (4, 8, 16):
+        for bps in (0, 1, 2, 3, 4, 6, 8):
+            if warps * bps > 64 or (bps and warps * bps < 8):
+                continue
+            bt.bt_tree_set_launch(tree.handle, warps, 16384)
+            bt.bt_tree_set_corun(tree.handle, bps, 0)
+            for i in range(4):
+                bt.bt_descend_sorted(tree.handle, *batches[i], B, v, f, None, s)
+            ev = []
+            for i in range(steps):
+                e0, e1 = _events()
+                e0.record(s)
+                bt.bt_descend_sorted(tree.handle, *batches[i % 4], B, v, f, None, s)
+                e1.record(s)
+                ev.append((e0, e1))
+            torch.cuda.synchronize()
+            us = statistics.median(1000 * a.elapsed_time(b) for a, b in ev)
+            print(f"{warps} warps per block, {bps or 'max'} blocks per SM: descent {us:.1f} us", flush=True)
+    tree.close()
+
+
 def main(argv=None) -> int:
     argv = sys.argv[1:] if argv is None else argv
-    if not argv or argv[0] not in ("forest", "keys32", "crossover"):
+    if not argv or argv[0] not in ("forest", "keys32", "crossover", "shapes"):
         print(__doc__)
         return 2
     if argv[0] == "forest":
         forest(*(int(x) for x in argv[1:5]))
     elif argv[0] == "keys32":
         keys32(*argv[1:2])
-    else:
+    elif argv[0] == "crossover":
         crossover()
+    else:
+        shapes()
     return 0
 
 
