@@ -1184,12 +1184,15 @@ def run_ours(a):
         e2e_s = reduce_max(sum(tt) / 1e3, world, device="cuda")
         serial = B * Ke * world / e2e_s
         # the same calls pipelined the way a host keeps a GPU busy (Sec. V-B,
-        # Fig. 7): three streams, each with its own pinned buffers and
-        # workspace, steps issued in turn, so one step's copies in, another's
-        # copies out and a third's kernels overlap (the host link, not the
-        # search, bounds this path); every step still copies its queries in
-        # and its values and found flags out.
-        NS = 3
+        # Fig. 7): four streams, each with its own pinned buffers and
+        # workspace, steps issued in turn, so that steps' copies in, copies
+        # out and kernels overlap; the launch shapes are capped as in the
+        # two-in-flight loop, so that one step's partition runs beside
+        # another's descent.  Every step still copies its queries in and its
+        # values and found flags out.
+        NS = 4
+        if a.streams == 2:
+            bt.bt_tree_set_corun(tree.handle, corun[0], corun[1])
         streams = [torch.cuda.Stream() for _ in range(NS)]
         bufs = []
         for j in range(NS):
@@ -1217,10 +1220,13 @@ def run_ours(a):
         p1.record(stream)
         torch.cuda.synchronize()
         pipe_s = reduce_max(p0.elapsed_time(p1) / 1e3, world, device="cuda")
+        bt.bt_tree_set_corun(tree.handle, 0, 0)
         pipelined = B * Ke * world / pipe_s
         line["e2e"] = {"value": pipelined, "unit": UNIT, "h2d_bytes_per_step": B * kb,
                        "d2h_bytes_per_step": B * (vb + 1), "steps": Ke,
-                       "entry_point": "bt_search_batch_host (pinned host buffers), three streams in turn",
+                       "entry_point": f"bt_search_batch_host (pinned host buffers), {NS} streams in turn"
+                                      + (f", launch shapes capped as in the two-in-flight loop {corun}"
+                                         if a.streams == 2 else ""),
                        "serial_value": serial, "serial_p50_us": 1e3 * sorted(tt)[len(tt) // 2],
                        "l2": "serial: flushed before every step; pipelined: not flushed (steps overlap; the "
                              "282 MB tree exceeds the 129 MB L2)"}
