@@ -23,6 +23,9 @@
  *   - `stream` is a CUDA runtime stream (cudaStream_t); NULL is the legacy
  *     default stream.  The header declares it as `struct CUstream_st *`, which
  *     is what cudaStream_t is, so that it needs no CUDA header.
+ *   - Device key, position and value arrays of the search, sort and descent
+ *     calls are aligned to their element size (32-byte keys: to 16 bytes);
+ *     a misaligned one is an argument error (BT_ERR_ARG).
  *   - Argument errors are returned synchronously and leave outputs untouched.
  *     Launch and runtime failures of the CUDA runtime are returned as
  *     BT_ERR_CUDA; bt_last_error_detail() then names the failing call.
@@ -230,8 +233,9 @@ bt_status bt_search_batch_ex(const bt_tree *tree, const void *d_queries, uint64_
  * unspecified (it follows device atomics and may differ between calls).
  * One cooperative kernel (coarse counts, scatter, per-bucket local sort,
  * with two bounded grid barriers; see bt_check_timeouts) after one memset of
- * the coarse-bucket counters; bt_sort_batch adds one kernel that writes the
- * two output arrays.
+ * the coarse-bucket counters; for integer keys bt_sort_batch adds one kernel
+ * that writes the two output arrays (32-byte keys are written into them by
+ * the partition itself).
  *
  *   d_queries         nq keys (device).
  *   d_sorted_queries  nq keys (device), must not overlap d_queries.
@@ -323,7 +327,7 @@ bt_status bt_search_batch_host(const bt_tree *tree, const void *h_queries, uint6
  * Errors: as bt_search_batch, plus BT_ERR_ARG for nq > BT_NOALLOC_MAX_QUERIES
  * and BT_ERR_WORKSPACE when the batch's scratch would exceed the array (it
  * does not at up to BT_NOALLOC_MAX_QUERIES queries: 65536 32-byte-key
- * queries need 3.7 MB, integer keys 1.1 MB).
+ * queries need 2.9 MB, integer keys 1.1 MB).
  */
 #define BT_NOALLOC_MAX_QUERIES 65536
 bt_status bt_search_batch_noalloc(const bt_tree *tree, const void *d_queries, uint64_t nq,

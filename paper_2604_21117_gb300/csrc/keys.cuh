@@ -93,9 +93,10 @@ __device__ __forceinline__ bool mem_lt<Key32>(const Key32 *p, const Key32 &key)
     return *p < key;
 }
 
-// One query of the partitioned batch: the key as the caller gave it, its
-// input position, and its local-sort digit (16 bytes for integer keys, 48
-// for 32-byte keys), so that each query moves with one vector store.
+// One query of a partitioned batch of integer keys: the key as the caller
+// gave it, its input position, and its local-sort digit, 16 bytes, so that
+// each query moves with one vector store.  (32-byte keys are partitioned
+// into separate key and position arrays.)
 template <typename K>
 struct alignas(16) PartRec {
     RawOf<K> key;

@@ -28,9 +28,10 @@
 //             counting), as one record (key, input position, digit) -- for
 //             32-byte keys as an 8-byte (position, digit) pair;
 //   sort      groups of threads order the coarse buckets by digit, in
-//             place (32-byte keys: from the pairs into the records, each
-//             key read from the batch once), several buckets per block at
-//             once.  Buckets of more
+//             place (32-byte keys: from the pairs into an array of the keys
+//             and an array of their positions, each key read from the batch
+//             once and written as one 32-byte sector), several buckets per
+//             block at once.  Buckets of more
 //             than part_tile<K>() queries (a hot key, or a coarse bucket far
 //             above its average size) keep the scatter's order.
 //
@@ -441,7 +442,9 @@ template <typename K>
 __global__ void __launch_bounds__(kPartThreads, 2) k_partition(const RawOf<K> *__restrict__ q, uint64_t nq,
                                                                PartNorm<K> pn, unsigned int *__restrict__ total,
                                                                uint32_t nb, PartRec<K> *__restrict__ rec,
-                                                               uint2 *__restrict__ pairs, uint32_t polls)
+                                                               uint2 *__restrict__ pairs,
+                                                               RawOf<K> *__restrict__ out_q,
+                                                               uint32_t *__restrict__ out_i, uint32_t polls)
 {
     __shared__ PartSmem<K> S;
     extern __shared__ __align__(16) unsigned char dsm[];
@@ -579,8 +582,8 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_partition(const RawOf<K> *_
     uint32_t *gtmp = gb + (1 << kLocalBits);  // per-warp partial sums of the group's scan
     constexpr int EL = part_tile<K>() / kSortThreads;
     if constexpr (part_narrow<K>()) {
-        // every bucket's pairs become records: sorted by digit when the
-        // bucket fits the tile, else in scatter order
+        // every bucket's pairs become keys and positions: sorted by digit
+        // when the bucket fits the tile, else in scatter order
         for (uint32_t b = grp * gridDim.x + blockIdx.x; b < nb; b += gridDim.x * kSortGroups) {
             const uint32_t bs = st[b];
             const uint32_t n = st[b + 1] - bs;
@@ -588,11 +591,8 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_partition(const RawOf<K> *_
             if (n > static_cast<uint32_t>(part_tile<K>()) || pn.lb == 0) {
                 for (uint32_t i = gtid; i < n; i += kSortThreads) {
                     const uint2 pr = __ldcg(pairs + bs + i);
-                    PartRec<K> r;
-                    r.key = q[pr.x];
-                    r.idx = pr.x;
-                    r.digit = pr.y;
-                    rec[bs + i] = r;
+                    out_q[bs + i] = q[pr.x];
+                    out_i[bs + i] = pr.x;
                 }
                 continue;
             }
@@ -618,11 +618,8 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_partition(const RawOf<K> *_
                 if (i < n) {
                     const uint32_t p = gb[pr[e].y & (nd - 1u)] + rk[e];
                     if (p < n) {  // always true; keeps a stray write inside the bucket
-                        PartRec<K> r;
-                        r.key = q[pr[e].x];
-                        r.idx = pr[e].x;
-                        r.digit = pr[e].y;
-                        rec[bs + p] = r;
+                        out_q[bs + p] = q[pr[e].x];
+                        out_i[bs + p] = pr[e].x;
                     }
                 }
             }
@@ -662,7 +659,8 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_partition(const RawOf<K> *_
     }
 }
 
-// The records split into a key array and a position array (bt_sort_batch).
+// The records split into a key array and a position array (bt_sort_batch,
+// integer keys).
 template <typename K>
 __global__ void k_part_unpack(const PartRec<K> *__restrict__ rec, uint64_t nq, RawOf<K> *__restrict__ out_q,
                               uint32_t *__restrict__ out_i)

@@ -49,10 +49,12 @@ static cudaError_t descend_any(const DescendArgs &a, cudaStream_t s)
     return descend_synchronous(a, s);
 }
 
+// view: the tree as the descent sees it (null: the tree itself).
 static cudaError_t descend(const bt_tree *tree, const void *q, const uint32_t *qidx, const void *recs, uint64_t nq,
-                           void *out_v, uint8_t *out_f, unsigned long long *fetch, cudaStream_t s)
+                           void *out_v, uint8_t *out_f, unsigned long long *fetch, cudaStream_t s,
+                           const DevTree *view = nullptr)
 {
-    const DescendArgs a{&tree->dev, tree, q, qidx, recs, nq, out_v, out_f, fetch, nullptr, nullptr};
+    const DescendArgs a{view ? view : &tree->dev, tree, q, qidx, recs, nq, out_v, out_f, fetch, nullptr, nullptr};
     return descend_any(a, s);
 }
 
@@ -71,7 +73,7 @@ __global__ void k_fill_miss(V *__restrict__ out_v, uint8_t *__restrict__ out_f, 
 static inline uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
 
 struct WsLayout {
-    uint64_t rec, pairs, counts, total;
+    uint64_t rec, ridx, pairs, counts, total;
 };
 
 // Coarse-bucket totals of the partition and its two grid-barrier counters:
@@ -81,17 +83,24 @@ constexpr uint64_t kPartCountWords = (1ull << kMaxCoarseBits) + 4;
 // Queries per partition block (at least).
 constexpr uint64_t kPartPerBlock = 2048;
 
-// Workspace: the partitioned batch (one record per query: key, input
-// position, local digit), for 32-byte keys the scattered (position, digit)
-// pairs the records are made from, and the partition's bucket totals and
-// barrier counters.
+// Workspace: the partitioned batch -- for integer keys one record per
+// query (key, input position, local digit), for 32-byte keys an array of
+// the keys (rec) and one of their input positions (ridx), made from the
+// scattered (position, digit) pairs -- and the partition's bucket totals
+// and barrier counters.
 static WsLayout ws_layout(int kb, uint64_t nq)
 {
     WsLayout w;
     uint64_t o = 0;
-    const uint64_t rb = kb > 8 ? sizeof(PartRec<Key32>) : sizeof(PartRec<uint64_t>);
     w.rec = o;
-    o = align256(o + nq * rb);
+    if (kb > 8) {
+        o = align256(o + nq * sizeof(Raw32));
+        w.ridx = o;
+        o = align256(o + nq * 4);
+    } else {
+        o = align256(o + nq * sizeof(PartRec<uint64_t>));
+        w.ridx = w.rec;
+    }
     w.pairs = o;
     if (kb > 8) o = align256(o + nq * 8);
     w.counts = o;
@@ -101,6 +110,17 @@ static WsLayout ws_layout(int kb, uint64_t nq)
 }
 
 static int bitlen(uint64_t x) { return x ? 64 - __builtin_clzll(x) : 0; }
+
+// Device arrays a search reads or writes are aligned to their element size
+// (32-byte keys: to 16 bytes, the width of the loads and stores that move
+// them); qidx and vals may be null (not checked).
+static bool arrays_aligned(const DevTree &t, const void *keys, const void *qidx, const void *vals)
+{
+    const uintptr_t ka = static_cast<uintptr_t>(t.key_bytes > 16 ? 16 : t.key_bytes);
+    const uintptr_t va = static_cast<uintptr_t>(t.val_bytes);
+    return (reinterpret_cast<uintptr_t>(keys) & (ka - 1)) == 0 && (reinterpret_cast<uintptr_t>(qidx) & 3u) == 0 &&
+           (reinterpret_cast<uintptr_t>(vals) & (va - 1)) == 0;
+}
 
 // Queries per batch from which the automatic choice partitions the batch,
 // for trees larger than a quarter of the L2 (DevTree::sort_pays).  Measured
@@ -186,9 +206,12 @@ void tree_bounds<Key32>(const DevTree &t, Key32 *lo, Key32 *hi)
 // Kernels the partition launches for a plan (plus one memset).
 static int part_kernels(const PartPlan &pp) { return pp.bits ? 1 : 0; }
 
+// out_q / out_i: where 32-byte keys' partitioned keys and positions go
+// (unused for integer keys, whose records stay in the workspace).
 template <typename K>
 static cudaError_t part_sort(const DevTree &t, const RawOf<K> *q, uint64_t nq, const PartPlan &pp,
-                             unsigned char *ws, const WsLayout &w, cudaStream_t s)
+                             unsigned char *ws, const WsLayout &w, RawOf<K> *out_q, uint32_t *out_i,
+                             cudaStream_t s)
 {
     PartNorm<K> pn;
     pn.split = static_cast<const K *>(t.split);
@@ -205,8 +228,12 @@ static cudaError_t part_sort(const DevTree &t, const RawOf<K> *q, uint64_t nq, c
     pn.p0 = t.split_p0;
     pn.wmin = t.split_wmin;
     unsigned int *total = reinterpret_cast<unsigned int *>(ws + w.counts);
-    PartRec<K> *rec = reinterpret_cast<PartRec<K> *>(ws + w.rec);
+    PartRec<K> *rec = part_narrow<K>() ? nullptr : reinterpret_cast<PartRec<K> *>(ws + w.rec);
     uint2 *pairs = part_narrow<K>() ? reinterpret_cast<uint2 *>(ws + w.pairs) : nullptr;
+    if (!part_narrow<K>()) {
+        out_q = nullptr;
+        out_i = nullptr;
+    }
     cudaError_t e = cudaMemsetAsync(total, 0, (static_cast<uint64_t>(pp.nb) + 4) * 4, s);
     if (e != cudaSuccess) return e;
     const void *kern = reinterpret_cast<const void *>(k_partition<K>);
@@ -225,36 +252,57 @@ static cudaError_t part_sort(const DevTree &t, const RawOf<K> *q, uint64_t nq, c
     if (g > cap) g = cap;
     if (g > kMaxPartBlocks) g = kMaxPartBlocks;
     uint32_t nb = pp.nb, polls = first_wait_polls();
-    void *args[] = {const_cast<RawOf<K> **>(&q), &nq, &pn, &total, &nb, &rec, &pairs, &polls};
+    void *args[] = {const_cast<RawOf<K> **>(&q), &nq, &pn, &total, &nb, &rec, &pairs, &out_q, &out_i, &polls};
     return cudaLaunchCooperativeKernel(kern, dim3(static_cast<unsigned>(g)), dim3(kPartThreads), args,
                                        static_cast<size_t>(dyn), s);
 }
 
-// Where the partitioned batch's records end up.
-static const unsigned char *part_records(const unsigned char *ws, const WsLayout &w, const PartPlan &pp)
+// Where the descent finds a partitioned batch: the workspace's records
+// (integer keys), or its key and position arrays (32-byte keys).
+struct PartOut {
+    const void *q;
+    const uint32_t *qidx;
+    const void *recs;
+};
+
+static PartOut part_output(const DevTree &t, const unsigned char *ws, const WsLayout &w)
 {
-    (void)pp;
-    return ws + w.rec;
+    if (t.key_bytes == 32) return {ws + w.rec, reinterpret_cast<const uint32_t *>(ws + w.ridx), nullptr};
+    return {nullptr, nullptr, ws + w.rec};
 }
 
-// The partition of a batch into the workspace's records.
+// The descent's view of a tree for a partitioned batch: inner-level staging
+// left to the library ("auto") is on, as for a batch given as records.
+static DevTree partitioned_view(const DevTree &t)
+{
+    DevTree v = t;
+    if (v.inner_stage == 2) v.inner_stage = 1;
+    return v;
+}
+
+// The partition of a batch into the workspace (32-byte keys: into out_q /
+// out_i when given, else the workspace's key and position arrays).
 static cudaError_t sort_any(const DevTree &t, const void *q, uint64_t nq, const PartPlan &pp,
-                            unsigned char *ws, const WsLayout &w, cudaStream_t s)
+                            unsigned char *ws, const WsLayout &w, cudaStream_t s, void *out_q = nullptr,
+                            uint32_t *out_i = nullptr)
 {
-    if (t.key_bytes == 32) return part_sort<Key32>(t, static_cast<const Raw32 *>(q), nq, pp, ws, w, s);
-    if (t.key_bytes == 8) return part_sort<uint64_t>(t, static_cast<const uint64_t *>(q), nq, pp, ws, w, s);
-    return part_sort<uint32_t>(t, static_cast<const uint32_t *>(q), nq, pp, ws, w, s);
+    if (t.key_bytes == 32) {
+        Raw32 *oq = out_q ? static_cast<Raw32 *>(out_q) : reinterpret_cast<Raw32 *>(ws + w.rec);
+        uint32_t *oi = out_i ? out_i : reinterpret_cast<uint32_t *>(ws + w.ridx);
+        return part_sort<Key32>(t, static_cast<const Raw32 *>(q), nq, pp, ws, w, oq, oi, s);
+    }
+    if (t.key_bytes == 8)
+        return part_sort<uint64_t>(t, static_cast<const uint64_t *>(q), nq, pp, ws, w, nullptr, nullptr, s);
+    return part_sort<uint32_t>(t, static_cast<const uint32_t *>(q), nq, pp, ws, w, nullptr, nullptr, s);
 }
 
-// The records split into the caller's key and position arrays.
+// The records of integer keys split into the caller's key and position
+// arrays.
 static cudaError_t unpack_any(const DevTree &t, const unsigned char *recs, uint64_t nq, void *dq, uint32_t *di,
                               cudaStream_t s)
 {
     const unsigned grid = static_cast<unsigned>((nq + 255) / 256 < 4096 ? (nq + 255) / 256 : 4096);
-    if (t.key_bytes == 32)
-        k_part_unpack<Key32><<<grid, 256, 0, s>>>(reinterpret_cast<const PartRec<Key32> *>(recs), nq,
-                                                  static_cast<Raw32 *>(dq), di);
-    else if (t.key_bytes == 8)
+    if (t.key_bytes == 8)
         k_part_unpack<uint64_t><<<grid, 256, 0, s>>>(reinterpret_cast<const PartRec<uint64_t> *>(recs), nq,
                                                      static_cast<uint64_t *>(dq), di);
     else
@@ -303,6 +351,7 @@ extern "C" bt_status bt_search_batch_ex(const bt_tree *tree, const void *d_queri
     if (nq == 0) return BT_OK;
     if (nq >= (1ull << 31)) return BT_ERR_ARG;
     if (!d_queries || !d_out_vals || !d_out_found) return BT_ERR_ARG;
+    if (!arrays_aligned(tree->dev, d_queries, nullptr, d_out_vals)) return BT_ERR_ARG;
     const DevTree &t = tree->dev;
     const WsLayout w = ws_layout(t.key_bytes, nq);
     if (!d_workspace || ws_bytes < w.total || (reinterpret_cast<uintptr_t>(d_workspace) & 255u))
@@ -326,16 +375,25 @@ extern "C" bt_status bt_search_batch_ex(const bt_tree *tree, const void *d_queri
 
     const PartPlan pp = plan_partition(t, opts ? opts->sort_bits : -1, nq);
     const void *q = d_queries;
+    const uint32_t *qidx = nullptr;
     const void *recs = nullptr;
     unsigned char *ws = static_cast<unsigned char *>(d_workspace);
+    DevTree pv;
+    const DevTree *view = nullptr;
     if (pp.bits > 0) {
         e = sort_any(t, d_queries, nq, pp, ws, w, s);
         if (e != cudaSuccess) {
             set_error_detail("batch partition launch", e);
             return BT_ERR_CUDA;
         }
-        q = nullptr;
-        recs = part_records(ws, w, pp);
+        const PartOut po = part_output(t, ws, w);
+        q = po.q;
+        qidx = po.qidx;
+        recs = po.recs;
+        if (!recs) {
+            pv = partitioned_view(t);
+            view = &pv;
+        }
     }
     if (opts && opts->phase_event) {
         e = cudaEventRecord(static_cast<cudaEvent_t>(opts->phase_event), s);
@@ -344,7 +402,7 @@ extern "C" bt_status bt_search_batch_ex(const bt_tree *tree, const void *d_queri
             return BT_ERR_CUDA;
         }
     }
-    e = descend(tree, q, nullptr, recs, nq, d_out_vals, d_out_found, opts ? opts->d_fetch_counts : nullptr, s);
+    e = descend(tree, q, qidx, recs, nq, d_out_vals, d_out_found, opts ? opts->d_fetch_counts : nullptr, s, view);
     if (e != cudaSuccess) {
         set_error_detail("descent launch", e);
         return BT_ERR_CUDA;
@@ -403,6 +461,9 @@ extern "C" bt_status bt_sort_batch(const bt_tree *tree, const void *d_queries, u
     if (nq == 0) return BT_OK;
     if (nq >= (1ull << 31)) return BT_ERR_ARG;
     if (!d_queries || !d_sorted_queries || !d_sorted_index) return BT_ERR_ARG;
+    if (!arrays_aligned(tree->dev, d_queries, d_sorted_index, nullptr) ||
+        !arrays_aligned(tree->dev, d_sorted_queries, nullptr, nullptr))
+        return BT_ERR_ARG;
     const DevTree &t = tree->dev;
     const WsLayout w = ws_layout(t.key_bytes, nq);
     if (!d_workspace || ws_bytes < w.total || (reinterpret_cast<uintptr_t>(d_workspace) & 255u))
@@ -426,8 +487,12 @@ extern "C" bt_status bt_sort_batch(const bt_tree *tree, const void *d_queries, u
         e = cudaGetLastError();
     } else {
         unsigned char *ws = static_cast<unsigned char *>(d_workspace);
-        e = sort_any(t, d_queries, nq, pp, ws, w, s);
-        if (e == cudaSuccess) e = unpack_any(t, part_records(ws, w, pp), nq, d_sorted_queries, d_sorted_index, s);
+        if (t.key_bytes == 32) {  // written straight into the caller's arrays
+            e = sort_any(t, d_queries, nq, pp, ws, w, s, d_sorted_queries, d_sorted_index);
+        } else {
+            e = sort_any(t, d_queries, nq, pp, ws, w, s);
+            if (e == cudaSuccess) e = unpack_any(t, ws + w.rec, nq, d_sorted_queries, d_sorted_index, s);
+        }
     }
     if (e != cudaSuccess) {
         set_error_detail("batch partition launch", e);
@@ -444,6 +509,7 @@ extern "C" bt_status bt_descend_sorted(const bt_tree *tree, const void *d_querie
     if (nq == 0) return BT_OK;
     if (nq >= (1ull << 31)) return BT_ERR_ARG;
     if (!d_queries || !d_out_vals || !d_out_found) return BT_ERR_ARG;
+    if (!arrays_aligned(tree->dev, d_queries, d_index, d_out_vals)) return BT_ERR_ARG;
     const DevTree &t = tree->dev;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e;
@@ -472,6 +538,7 @@ extern "C" bt_status bt_learned_descend_sorted(const bt_tree *tree, const bt_mod
     if (nq == 0) return BT_OK;
     if (nq >= (1ull << 31)) return BT_ERR_ARG;
     if (!d_queries || !d_out_vals || !d_out_found) return BT_ERR_ARG;
+    if (!arrays_aligned(tree->dev, d_queries, d_index, d_out_vals)) return BT_ERR_ARG;
     const DevTree &t = tree->dev;
     if (t.height == 0 || model->dev.leaves != t.nodes[t.height - 1]) return BT_ERR_ARG;
     const DescendArgs a{&t, tree, d_queries, d_index, nullptr, nq, d_out_vals, d_out_found, nullptr, &model->dev,
@@ -492,6 +559,7 @@ extern "C" bt_status bt_learned_search_batch(const bt_tree *tree, const bt_model
     if (nq == 0) return BT_OK;
     if (nq >= (1ull << 31)) return BT_ERR_ARG;
     if (!d_queries || !d_out_vals || !d_out_found) return BT_ERR_ARG;
+    if (!arrays_aligned(tree->dev, d_queries, nullptr, d_out_vals)) return BT_ERR_ARG;
     const DevTree &t = tree->dev;
     if (t.height == 0 || model->dev.leaves != t.nodes[t.height - 1]) return BT_ERR_ARG;
     const WsLayout w = ws_layout(t.key_bytes, nq);
@@ -500,6 +568,7 @@ extern "C" bt_status bt_learned_search_batch(const bt_tree *tree, const bt_model
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const PartPlan pp = plan_partition(t, -1, nq);
     const void *q = d_queries;
+    const uint32_t *qidx = nullptr;
     const void *recs = nullptr;
     unsigned char *ws = static_cast<unsigned char *>(d_workspace);
     cudaError_t e;
@@ -509,10 +578,12 @@ extern "C" bt_status bt_learned_search_batch(const bt_tree *tree, const bt_model
             set_error_detail("batch partition launch", e);
             return BT_ERR_CUDA;
         }
-        q = nullptr;
-        recs = part_records(ws, w, pp);
+        const PartOut po = part_output(t, ws, w);
+        q = po.q;
+        qidx = po.qidx;
+        recs = po.recs;
     }
-    const DescendArgs a{&t, tree, q, nullptr, recs, nq, d_out_vals, d_out_found, nullptr, &model->dev, nullptr};
+    const DescendArgs a{&t, tree, q, qidx, recs, nq, d_out_vals, d_out_found, nullptr, &model->dev, nullptr};
     e = descend_any(a, s);
     if (e != cudaSuccess) {
         set_error_detail("learned descent launch", e);
@@ -547,6 +618,7 @@ extern "C" bt_status bt_paper_descend_sorted(const bt_tree *tree, const void *d_
     if (nq == 0) return BT_OK;
     if (nq >= (1ull << 31)) return BT_ERR_ARG;
     if (!d_queries || !d_out_vals || !d_out_found) return BT_ERR_ARG;
+    if (!arrays_aligned(tree->dev, d_queries, d_index, d_out_vals)) return BT_ERR_ARG;
     if (tree->dev.height > 0 && !tree->d_paper) return BT_ERR_ARG;
     if (tree->dev.height == 0) return bt_descend_sorted(tree, d_queries, d_index, nq, d_out_vals, d_out_found,
                                                         nullptr, stream);
@@ -567,6 +639,7 @@ extern "C" bt_status bt_paper_search_batch(const bt_tree *tree, const void *d_qu
     if (nq == 0) return BT_OK;
     if (nq >= (1ull << 31)) return BT_ERR_ARG;
     if (!d_queries || !d_out_vals || !d_out_found) return BT_ERR_ARG;
+    if (!arrays_aligned(tree->dev, d_queries, nullptr, d_out_vals)) return BT_ERR_ARG;
     const DevTree &t = tree->dev;
     if (t.height > 0 && !tree->d_paper) return BT_ERR_ARG;
     if (t.height == 0)
@@ -577,6 +650,7 @@ extern "C" bt_status bt_paper_search_batch(const bt_tree *tree, const void *d_qu
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const PartPlan pp = plan_partition(t, -1, nq);
     const void *q = d_queries;
+    const uint32_t *qidx = nullptr;
     const void *recs = nullptr;
     unsigned char *ws = static_cast<unsigned char *>(d_workspace);
     cudaError_t e;
@@ -586,10 +660,12 @@ extern "C" bt_status bt_paper_search_batch(const bt_tree *tree, const void *d_qu
             set_error_detail("batch partition launch", e);
             return BT_ERR_CUDA;
         }
-        q = nullptr;
-        recs = part_records(ws, w, pp);
+        const PartOut po = part_output(t, ws, w);
+        q = po.q;
+        qidx = po.qidx;
+        recs = po.recs;
     }
-    e = descend_paper_layout(t, tree->paper, q, nullptr, recs, nq, d_out_vals, d_out_found, s);
+    e = descend_paper_layout(t, tree->paper, q, qidx, recs, nq, d_out_vals, d_out_found, s);
     if (e != cudaSuccess) {
         set_error_detail("paper-layout descent launch", e);
         return BT_ERR_CUDA;

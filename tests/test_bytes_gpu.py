@@ -105,6 +105,7 @@ def test_bulk_staging(bt, m):
     q = W.make_byte_queries(keys, 30_001, 0.6, seed=931)
     _check(bt, tree, o, q, -1)
     _check(bt, tree, o, q, 0)
+    _check(bt, tree, o, q, 16)
     bt.bt_check_timeouts()
 
 
@@ -116,7 +117,9 @@ def test_launch_settings(bt, warps, pin, lq):
     bt.bt_tree_set_launch(tree.handle, warps, pin)
     bt.bt_tree_set_lane_queries(tree.handle, lq)
     o = OracleBytesTree(keys, vals, 16)
-    _check(bt, tree, o, W.make_byte_queries(keys, 25_000, 0.6, seed=941))
+    q = W.make_byte_queries(keys, 25_000, 0.6, seed=941)
+    _check(bt, tree, o, q)
+    _check(bt, tree, o, q, 16)
 
 
 def test_device_layout_is_big_endian_words(bt):
@@ -192,3 +195,64 @@ def test_unsupported_uses_are_refused(bt):
         bt.bt_model_train(tree.handle, bt.BT_MODEL_PL, segments=16)
     with pytest.raises(bt.BTreeError):
         bt.bt_forest_create([tree])
+
+
+@pytest.mark.slow
+def test_paper_tree_full_batch(bt):
+    """The paper's own tree (2^20 distinct 32-byte keys, 8-byte values,
+    fanout 16) and a batch of 2^20 queries at 90% hits: the automatic choice
+    partitions it (the tree's image is larger than a quarter of the L2), and
+    every result, through both node layouts, equals the byte-key oracle."""
+    import torch
+    n = nq = 1 << 20
+    keys = W.byte_keys(n, 32, seed=W.SEED_BASE + 8)
+    vals = W.rank_values(n, 64)
+    tree = bt.BTree(keys, vals, 16)
+    o = OracleBytesTree(keys, vals, 16)
+    q = W.make_byte_queries(keys, nq, 0.9, seed=W.SEED_BASE + 9 + nq)
+    assert bt.bt_sort_bits(tree.handle, nq, -1) == 20
+    _check(bt, tree, o, q, -1)
+    bt.bt_paper_layout_build(tree.handle)
+    v, f = tree.alloc_outputs(nq)
+    ws, nb = tree.alloc_workspace(nq)
+    bt.bt_paper_search_batch(tree.handle, _dev(q), nq, v, f, ws, nb)
+    ov, of, _, _ = o.search(q)
+    assert np.array_equal(v.cpu().numpy(), ov) and np.array_equal(f.cpu().numpy(), of)
+    torch.cuda.synchronize()
+    o.close()
+    tree.close()
+
+
+def test_misaligned_arrays_are_refused(bt):
+    """32-byte keys move as 16-byte pieces: a key array that is not 16-byte
+    aligned is refused on the host (BT_ERR_ARG) before anything is launched,
+    by the search, the sort and the descent; so is a misaligned value array."""
+    import torch
+    keys = W.byte_keys(5000, 32, seed=990)
+    tree = bt.BTree(keys, W.rank_values(keys.shape[0], 64), 16)
+    nq = 1000
+    buf = torch.zeros((nq + 1) * 32, dtype=torch.uint8, device="cuda")
+    base = buf.data_ptr()
+    assert base % 256 == 0
+    v, f = tree.alloc_outputs(nq)
+    ws, nb = tree.alloc_workspace(nq)
+    si = torch.empty(nq, dtype=torch.int32, device="cuda")
+    # every misaligned pointer still has room for the whole array after it
+    obuf = torch.zeros((nq + 1) * 32, dtype=torch.uint8, device="cuda")
+    vbuf = torch.zeros(nq + 1, dtype=torch.uint64, device="cuda")
+    ibuf = torch.zeros(nq + 1, dtype=torch.int32, device="cuda")
+    for call in (
+        lambda: bt.bt_search_batch(tree.handle, base + 8, nq, v, f, ws, nb),
+        lambda: bt.bt_search_batch(tree.handle, base, nq, vbuf.data_ptr() + 4, f, ws, nb),
+        lambda: bt.bt_sort_batch(tree.handle, base + 8, nq, 16, obuf, si, ws, nb),
+        lambda: bt.bt_sort_batch(tree.handle, base, nq, 16, obuf.data_ptr() + 8, si, ws, nb),
+        lambda: bt.bt_descend_sorted(tree.handle, base + 8, si, nq, v, f),
+        lambda: bt.bt_descend_sorted(tree.handle, base, ibuf.data_ptr() + 2, nq, v, f),
+    ):
+        with pytest.raises(bt.BTreeError) as e:
+            call()
+        assert e.value.code == "BT_ERR_ARG"
+    # the aligned calls on the same buffers go through
+    bt.bt_search_batch(tree.handle, base, nq, v, f, ws, nb)
+    torch.cuda.synchronize()
+    tree.close()

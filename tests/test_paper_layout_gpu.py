@@ -1,6 +1,7 @@
 """The paper's node layout (Eq. 1: header, keys, child addresses or data in
 one node, BFS order) searched on the GPU: bit-exact against the oracles for
-every key width and fanout, with and without the partition."""
+every key width and fanout, on the batch as given and on the batch
+partitioned by bt_sort_batch."""
 from __future__ import annotations
 
 import numpy as np
@@ -32,6 +33,12 @@ def _run(bt, tree, q, nq):
     v2, f2 = tree.alloc_outputs(nq)
     bt.bt_paper_descend_sorted(tree.handle, dq, None, nq, v2, f2)  # unsorted order
     assert np.array_equal(v2.cpu().numpy(), pv) and np.array_equal(f2.cpu().numpy(), pf)
+    sq = torch.empty_like(dq)
+    si = torch.empty(nq, dtype=torch.int32, device="cuda")
+    bt.bt_sort_batch(tree.handle, dq, nq, 16, sq, si, ws, nb)
+    v3, f3 = tree.alloc_outputs(nq)
+    bt.bt_paper_descend_sorted(tree.handle, sq, si, nq, v3, f3)  # partitioned, results in input order
+    assert np.array_equal(v3.cpu().numpy(), pv) and np.array_equal(f3.cpu().numpy(), pf)
     return pv, pf
 
 
