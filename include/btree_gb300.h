@@ -161,11 +161,11 @@ typedef struct bt_search_opts {
     /* Bits of the bucket number the batch is partitioned on before the
      * descent (Sec. IV-A sorts the batch so that queries for one node are
      * adjacent; see bt_sort_batch for the order obtained): -1 lets the
-     * library choose (none below 786432 queries, and none for a tree whose
-     * device image is at most a quarter of the L2: the partition pays for
-     * itself only when the batch is large and leaf blocks do not stay in the
-     * L2 between batches), 0 skips the partition,
-     * 1..21 forces that many bits (larger values mean 21). */
+     * library choose (none below 786432 queries -- 393216 for 32-byte
+     * keys -- and none for a tree whose device image is at most a quarter of
+     * the L2: the partition pays for itself only when the batch is large and
+     * leaf blocks do not stay in the L2 between batches), 0 skips the
+     * partition, 1..21 forces that many bits (larger values mean 21). */
     int32_t sort_bits;
     /* If non-NULL: device array of `height` counters to which the search
      * adds, per level, how many node key blocks it fetched -- the quantity
@@ -215,8 +215,9 @@ bt_status bt_search_batch_ex(const bt_tree *tree, const void *d_queries, uint64_
  * in the key, on `bits` bits: sort_bits when positive (values above 21 mean
  * 21), none for 0 (the queries are copied and the index is the identity),
  * and for -1 the library's choice, which bt_sort_bits reports (none below
- * 786432 queries or for a tree whose device image is at most a quarter of
- * the L2; otherwise coarse buckets of 512 to 1023 queries on average):
+ * 786432 queries (393216 for 32-byte keys) or for a tree whose device image
+ * is at most a quarter of the L2; otherwise coarse buckets of 512 to 1023
+ * queries on average):
  *   f(q) = (c << r) | s, where c = the number of the tree's splitters
  *   (bt_info.nsplit keys, see bt_build) smaller than q, and s = the fp32
  *   product (q - lo) * inv_c * 2^r truncated and clamped to [0, 2^r - 1],

@@ -130,6 +130,11 @@ static bool arrays_aligned(const DevTree &t, const void *keys, const void *qidx,
 // 79 against 82 at 2^20); on 10^6 keys (17 MB) the unsorted descent is faster
 // at every size to 2^20 (61 against 72 us there).
 constexpr uint64_t kAutoSortMinBatch = 786432;
+// The same for 32-byte keys, whose comparisons and 512-byte node blocks make
+// the unsorted descent dearer: on 2^20 keys at fanout 16 (47 MB) the sorted
+// search is faster from 2^19 queries (70 against 73 us with the L2 warm, 75
+// against 82 flushed), the unsorted one at 2^18 (43 against 47 us).
+constexpr uint64_t kAutoSortMinBatch32 = 393216;
 // Automatic bits: coarse buckets of 512 to 1023 queries on average, each
 // ordered by kLocalBits more bits -- finer than one leaf per query at every
 // configured batch size; at least 2 buckets and at most 2^kMaxCoarseBits,
@@ -166,13 +171,17 @@ struct PartPlan {
 };
 
 // sort_bits < 0: auto_part_bits for batches of at least kAutoSortMinBatch
-// queries over trees larger than a quarter of the L2, else none; sort_bits > 0: that many
+// queries (kAutoSortMinBatch32 for 32-byte keys) over trees larger than a
+// quarter of the L2, else none; sort_bits > 0: that many
 // bits, at most kMaxPartBits.
 static PartPlan plan_partition(const DevTree &t, int32_t sort_bits, uint64_t nq)
 {
     PartPlan p{0, 0, 0, 0, 0};
     int bits = sort_bits;
-    if (bits < 0) bits = (t.sort_pays && nq >= kAutoSortMinBatch) ? auto_part_bits(t.key_bytes, nq) : 0;
+    if (bits < 0) {
+        const uint64_t min_nq = t.key_bytes == 32 ? kAutoSortMinBatch32 : kAutoSortMinBatch;
+        bits = (t.sort_pays && nq >= min_nq) ? auto_part_bits(t.key_bytes, nq) : 0;
+    }
     if (bits > kMaxPartBits) bits = kMaxPartBits;
     if (bits <= 0 || t.height == 0) return p;
     const int cbits = bitlen(t.nsplit);  // c is in [0, nsplit]

@@ -201,7 +201,8 @@ def test_unsupported_uses_are_refused(bt):
 def test_paper_tree_full_batch(bt):
     """The paper's own tree (2^20 distinct 32-byte keys, 8-byte values,
     fanout 16) and a batch of 2^20 queries at 90% hits: the automatic choice
-    partitions it (the tree's image is larger than a quarter of the L2), and
+    partitions it (the tree's image is larger than a quarter of the L2 and
+    the batch above the 32-byte keys' threshold), and
     every result, through both node layouts, equals the byte-key oracle."""
     import torch
     n = nq = 1 << 20
@@ -211,6 +212,8 @@ def test_paper_tree_full_batch(bt):
     o = OracleBytesTree(keys, vals, 16)
     q = W.make_byte_queries(keys, nq, 0.9, seed=W.SEED_BASE + 9 + nq)
     assert bt.bt_sort_bits(tree.handle, nq, -1) == 20
+    # 32-byte keys are partitioned automatically from 393216 queries
+    assert bt.bt_sort_bits(tree.handle, 393215, -1) == 0 and bt.bt_sort_bits(tree.handle, 393216, -1) > 9
     _check(bt, tree, o, q, -1)
     bt.bt_paper_layout_build(tree.handle)
     v, f = tree.alloc_outputs(nq)
