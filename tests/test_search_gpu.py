@@ -220,6 +220,7 @@ def test_full_size_2p24_keys_fanout32(bt, zipf):
     vals = W.rank_values(n, 64)
     tree = bt.BTree(keys, vals, 32)
     assert tree.level_nodes == [1, 17, 529, 16913, 541201]
+    assert bt.bt_sort_bits(tree.handle, 786431, -1) == 0 and bt.bt_sort_bits(tree.handle, 786432, -1) > 9
     o = OracleTree(keys, vals, 32)
     for b in (1, 16, 64, 256, 1024, 1 << 20):
         q = W.make_queries(keys, b, 0.9, seed=W.SEED_BASE + 1000 + b, width_bits=64, zipf_s=zipf)
