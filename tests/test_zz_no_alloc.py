@@ -48,8 +48,9 @@ def test_noalloc_matches_workspace_entry_point_on_two_calls(bt):
 
 def test_noalloc_32_byte_keys_at_its_limit_against_the_oracle(bt):
     """The largest no-allocation batch of the paper's 32-byte keys (the
-    workspace it asks for, sized for a partition's pairs and records, fits
-    the scratch), every result against the byte-key oracle."""
+    workspace it asks for, sized for a partition's pairs, keys and
+    positions, fits the scratch), every result against the byte-key
+    oracle."""
     import torch
     from oracle.bytes_keys import OracleBytesTree
     keys = W.byte_keys(200_000, 32, seed=35)
