@@ -636,6 +636,14 @@ extern "C" bt_status bt_forest_get_launch(const bt_forest *f, bt_forest_tune *ou
     return BT_OK;
 }
 
+// The work list, queries and values are aligned to their element sizes.
+static bool forest_arrays_aligned(const bt_forest *f, const void *d_batches, const void *q, const void *v)
+{
+    const uintptr_t kb = static_cast<uintptr_t>(f->key_bytes), vb = static_cast<uintptr_t>(f->val_bytes);
+    return (reinterpret_cast<uintptr_t>(d_batches) & 7u) == 0 && (reinterpret_cast<uintptr_t>(q) & (kb - 1)) == 0 &&
+           (reinterpret_cast<uintptr_t>(v) & (vb - 1)) == 0;
+}
+
 extern "C" bt_status bt_forest_search(const bt_forest *f, const bt_batch_desc *d_batches, uint32_t nbatches,
                                       const void *d_queries, uint64_t nq, void *d_out_vals, uint8_t *d_out_found,
                                       void *d_workspace, uint64_t ws_bytes, uint32_t warps_per_block,
@@ -644,6 +652,7 @@ extern "C" bt_status bt_forest_search(const bt_forest *f, const bt_batch_desc *d
     if (!f) return BT_ERR_ARG;
     if (nbatches == 0) return BT_OK;
     if (!d_batches || !d_queries || !d_out_vals || !d_out_found) return BT_ERR_ARG;
+    if (!forest_arrays_aligned(f, d_batches, d_queries, d_out_vals)) return BT_ERR_ARG;
     if (warps_per_block == 0) warps_per_block = f->warps;
     if (warps_per_block > 16) return BT_ERR_ARG;
     if (!d_workspace || ws_bytes < bt_forest_workspace_bytes(nbatches)) return BT_ERR_WORKSPACE;
@@ -662,6 +671,7 @@ extern "C" bt_status bt_forest_autotune(bt_forest *f, const bt_batch_desc *d_bat
                                         void *d_workspace, uint64_t ws_bytes, bt_stream stream, bt_forest_tune *best)
 {
     if (!f || !best || nbatches == 0 || !d_batches || !d_queries || !d_out_vals || !d_out_found) return BT_ERR_ARG;
+    if (!forest_arrays_aligned(f, d_batches, d_queries, d_out_vals)) return BT_ERR_ARG;
     if (!d_workspace || ws_bytes < bt_forest_workspace_bytes(nbatches)) return BT_ERR_WORKSPACE;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaEvent_t e0 = nullptr, e1 = nullptr;

@@ -277,6 +277,10 @@ extern "C" bt_status bt_range_search(const bt_range *r, const void *d_queries, u
     if (!r) return BT_ERR_ARG;
     if (nq == 0) return BT_OK;
     if (nq >= (1ull << 31) || !d_queries || !d_out_vals || !d_out_found) return BT_ERR_ARG;
+    // queries and values aligned to their element sizes
+    if ((reinterpret_cast<uintptr_t>(d_queries) & static_cast<uintptr_t>(r->key_bytes - 1)) ||
+        (reinterpret_cast<uintptr_t>(d_out_vals) & static_cast<uintptr_t>(r->val_bytes - 1)))
+        return BT_ERR_ARG;
     const RangeWs w = range_ws(r, nq);
     if (!d_workspace || ws_bytes < w.bytes || (reinterpret_cast<uintptr_t>(d_workspace) & 255u))
         return BT_ERR_WORKSPACE;

@@ -324,3 +324,32 @@ def test_forest_every_key_and_value_width(bt, kw, vw, learned):
     bt.bt_forest_free(forest)
     for m in models or ():
         bt.bt_model_free(m)
+
+
+def test_misaligned_arrays_are_refused(bt):
+    """A work list, query array or value array that is not aligned to its
+    element size is refused on the host (BT_ERR_ARG), before any launch."""
+    import torch
+    trees, _, desc, _, allq, d_desc = _forest_case(bt, [5000], [16], 20, seed=3100)
+    forest = bt.bt_forest_create(trees)
+    n = allq.size
+    # byte buffers; every misaligned pointer still has room for the whole
+    # array after it
+    qbuf = torch.zeros((n + 1) * 8, dtype=torch.uint8, device="cuda")
+    qbuf[:n * 8].copy_(torch.from_numpy(allq.view(np.uint8)))
+    vbuf = torch.zeros((n + 1) * 8, dtype=torch.uint8, device="cuda")
+    dbuf = torch.zeros(d_desc.numel() + 16, dtype=torch.uint8, device="cuda")
+    dbuf[:d_desc.numel()].copy_(d_desc)
+    f = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    wsb = bt.bt_forest_workspace_bytes(desc.size)
+    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    dp, qp, vp = dbuf.data_ptr(), qbuf.data_ptr(), vbuf.data_ptr()
+    for dd, q, v in ((dp, qp + 4, vp), (dp, qp, vp + 4), (dp + 4, qp, vp)):
+        with pytest.raises(bt.BTreeError) as e:
+            bt.bt_forest_search(forest, dd, desc.size, q, v, f, ws, wsb, nq=n)
+        assert e.value.code == "BT_ERR_ARG"
+    bt.bt_forest_search(forest, dp, desc.size, qp, vp, f, ws, wsb, nq=n)
+    torch.cuda.synchronize()
+    bt.bt_forest_free(forest)
+    for t in trees:
+        t.close()

@@ -78,3 +78,24 @@ def test_range_build_checks(bt):
     with pytest.raises(bt.BTreeError) as e:
         bt.bt_range_build(keys[::-1].copy(), vals, 16, 2)
     assert e.value.code in ("BT_ERR_UNSORTED",)
+
+
+def test_range_search_refuses_misaligned_arrays(bt):
+    """A query or value array that is not aligned to its element size is
+    refused on the host (BT_ERR_ARG), before any launch."""
+    import torch
+    keys = W.uniform_keys(10_000, 64, seed=730)
+    r = bt.bt_range_build(keys, W.rank_values(keys.size, 64), 16, 4)
+    nq = 1000
+    qbuf = torch.zeros((nq + 1) * 8, dtype=torch.uint8, device="cuda")
+    vbuf = torch.zeros((nq + 1) * 8, dtype=torch.uint8, device="cuda")
+    f = torch.zeros(nq, dtype=torch.uint8, device="cuda")
+    nb = bt.bt_range_workspace_bytes(r, nq)
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    for q, v in ((qbuf.data_ptr() + 4, vbuf.data_ptr()), (qbuf.data_ptr(), vbuf.data_ptr() + 4)):
+        with pytest.raises(bt.BTreeError) as e:
+            bt.bt_range_search(r, q, nq, v, f, ws, nb)
+        assert e.value.code == "BT_ERR_ARG"
+    bt.bt_range_search(r, qbuf.data_ptr(), nq, vbuf.data_ptr(), f, ws, nb)
+    torch.cuda.synchronize()
+    bt.bt_range_free(r)
