@@ -45,13 +45,10 @@ METRIC = "batched B+tree lookups/s at 2^24 keys, learned vs plain; p99 µs; HBM 
 UNIT = "lookups/s"
 L2_FLUSH_BYTES = 256 << 20
 
-# DRAM bytes of one descent launch on the default workload, from one ncu
-# capture (dram__bytes_read.sum + dram__bytes_write.sum), valid only while
-# the kernel source is the one captured (sha256 prefix of csrc/search.cu).
 # DRAM bytes (read + write) of one k_descend launch on the default workload,
 # from one ncu capture of it (summarised under profiles/); valid only while
 # the descent's source (desc_pipe.cu and descent.cuh) hashes to the same value.
-NCU_DESCEND_TRAFFIC = {"descend_src_sha256": "5a7a4ccffe096dcb", "bytes_per_launch": 223773184}
+NCU_DESCEND_TRAFFIC = {"descend_src_sha256": "1b6f519f65890747", "bytes_per_launch": 223246592}
 
 
 def parse_args(argv=None):

@@ -452,13 +452,17 @@ typedef struct bt_tune {
 } bt_tune;
 
 /* Set the descent launch parameters of a built tree (not thread-safe with
- * searches running on it).  BT_ERR_ARG on unsupported values. */
+ * searches running on it): warps per descent block (1..16) and the bytes of
+ * top levels each block keeps in shared memory (0..49152).  The pipelined
+ * descent gives a batch with fewer 32-query chunks per SM than
+ * warps_per_block smaller blocks (that many warps, at least 2), so that a
+ * small batch spreads over more SMs.  BT_ERR_ARG on unsupported values. */
 bt_status bt_tree_set_launch(bt_tree *tree, uint32_t warps_per_block, uint32_t pin_bytes);
 
 /* How the descent stages node blocks into shared memory (Sec. IV-A: every
  * node a group of queries needs is loaded once):
  *   BT_STAGE_PIPELINED (the default): leaf blocks are staged by one
- *     asynchronous bulk copy each (the copy engine), completing on the warp's
+ *     asynchronous bulk copy each (the TMA unit), completing on the warp's
  *     mbarrier while the warp walks the next 32 queries down the inner
  *     levels; the wait is bounded (see bt_check_timeouts);
  *   BT_STAGE_CP_ASYNC: every level below the pinned ones is staged with

@@ -483,7 +483,17 @@ static cudaError_t launch_pipe(const DescendArgs &a, cudaStream_t s)
     DevTree t = *a.t;
     const bool istage = !LEARN && (t.inner_stage == 1 || (t.inner_stage == 2 && a.recs != nullptr));
     t.inner_stage = istage ? 1 : 0;
-    const int nw = t.warps > 0 ? t.warps : kDescWarpsDefault;
+    int nw = t.warps > 0 ? t.warps : kDescWarpsDefault;
+    // A batch with fewer 32-query chunks per SM than the tree's warps per
+    // block would sit on a few SMs: its blocks get that many warps (at least
+    // two), so that it spreads over more SMs (batch 1024: 6.3 us a call back
+    // to back at 2 warps per block against 6.7 at 8).
+    int sms = 0;
+    cudaError_t e = dev_sm_count(&sms);
+    if (e != cudaSuccess) return e;
+    if (sms < 1) sms = 1;
+    const uint64_t per_sm = ((a.nq + 31) / 32 + static_cast<uint64_t>(sms) - 1) / static_cast<uint64_t>(sms);
+    if (per_sm < static_cast<uint64_t>(nw)) nw = per_sm < 2 ? (nw < 2 ? nw : 2) : static_cast<int>(per_sm);
     ModelDev none;
     memset(&none, 0, sizeof(none));
     const ModelDev &md = a.md ? *a.md : none;
@@ -491,8 +501,8 @@ static cudaError_t launch_pipe(const DescendArgs &a, cudaStream_t s)
     const int smem = static_cast<int>(t.pin_bytes) + mbytes + nw * pipe_smem_per_warp<K, M, LEARN>(istage);
     auto kern = k_descend<K, V, M, COUNT, MODEL>;
     constexpr int max_model = LEARN ? static_cast<int>(kModelSmemSegments) * 20 : 0;
-    cudaError_t e = ensure_dyn_smem(reinterpret_cast<const void *>(kern),
-                                    kPinBudgetMax + max_model + kDescWarpsMax * pipe_smem_per_warp<K, M, LEARN>(true));
+    e = ensure_dyn_smem(reinterpret_cast<const void *>(kern),
+                        kPinBudgetMax + max_model + kDescWarpsMax * pipe_smem_per_warp<K, M, LEARN>(true));
     if (e != cudaSuccess) return e;
     unsigned grid = 0;
     e = persistent_grid(reinterpret_cast<const void *>(kern), nw * 32, smem, static_cast<uint64_t>(nw) * 32, a.nq,

@@ -45,7 +45,7 @@ __device__ __forceinline__ void prefetch_l1(const void *p)
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
-// ---- bulk asynchronous copies (the copy engine, non-tensor form) with an mbarrier ----
+// ---- bulk asynchronous copies (the TMA unit, non-tensor form) with an mbarrier ----
 
 // Bounded waits that gave up (the results of that search are invalid), and
 // give-ups after which the warp's copies had still not landed; read and
