@@ -85,6 +85,10 @@ static inline int key_cmp(const void *h_keys, uint64_t a, uint64_t b, int kb)
 namespace {
 std::mutex g_launch_mu;
 std::map<int, int> g_sms;                                           // device -> SMs
+// The same counts for the first devices, read without the lock on every
+// launch (0 until known).
+constexpr int kSmsFast = 64;
+std::atomic<int> g_sms_fast[kSmsFast];
 std::map<std::tuple<int, const void *, int, int>, int> g_occ;       // (device, kernel, threads, smem)
 std::map<std::pair<int, const void *>, int> g_dyn;                  // (device, kernel) -> limit set
 std::atomic<uint32_t> g_first_wait_polls{BT_DEFAULT_WAIT_POLLS};
@@ -97,6 +101,13 @@ cudaError_t dev_sm_count(int *sms)
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < kSmsFast) {
+        const int v = g_sms_fast[dev].load(std::memory_order_relaxed);
+        if (v > 0) {
+            *sms = v;
+            return cudaSuccess;
+        }
+    }
     std::lock_guard<std::mutex> lk(g_launch_mu);
     auto it = g_sms.find(dev);
     if (it == g_sms.end()) {
@@ -106,6 +117,7 @@ cudaError_t dev_sm_count(int *sms)
         it = g_sms.emplace(dev, v).first;
     }
     *sms = it->second;
+    if (dev >= 0 && dev < kSmsFast) g_sms_fast[dev].store(it->second, std::memory_order_relaxed);
     return cudaSuccess;
 }
 
