@@ -446,19 +446,34 @@ def designs_leg(a, bt, tree, dq, out_v, out_f, ws, nb, stream, alg, pool, steps:
 
 # ------------------------------------------------------ learned leg
 
-def _time_calls(fn, steps, flush, stream):
-    """Per-call CUDA-event times (us) of fn(), L2 flushed before each call."""
+# Device cycles of the spin each small timed call is queued behind (about
+# 50 us at 2 GHz: longer than the host takes to submit the call).
+SPIN_CYCLES = 100_000
+
+
+def _time_calls(fn, steps, flush, stream, submit=False):
+    """Per-call CUDA-event times (us) of fn(): the device's time for the call.
+    With `flush`, the L2 is flushed before each call (the 256 MB write also
+    keeps the device busy while the host submits the call); without it each
+    call is queued behind a short device spin, so that the host's submission
+    falls outside the timed region.  submit=True times without the spin:
+    submission plus device time, as a caller that waits on each call sees."""
     import torch
     out = []
-    for i in range(steps):
-        if flush is not None:
-            flush.fill_(i)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        fn()
-        e1.record(stream)
-        out.append((e0, e1))
+    with torch.cuda.stream(stream):
+        for i in range(steps):
+            if flush is not None:
+                flush.fill_(i)
+            elif not submit:
+                torch.cuda._sleep(SPIN_CYCLES)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            out.append((e0, e1))
+            if flush is None and i % 50 == 49:
+                torch.cuda.synchronize()  # keeps the queue of spins short
     torch.cuda.synchronize()
     return sorted(1e3 * x.elapsed_time(y) for x, y in out)
 
@@ -625,8 +640,9 @@ def sweep_leg(a, bt, stream, keys, vals, tree):
     """The configured sweeps: batch sizes 1, 16, 64, 256, 1024 and 2^20 on the
     2^24-key tree (uniform and Zipf(1.1) queries, 90% hits), and tree sizes
     10 to 2e7 keys (fanout 32) at batch 1024.  Lookups/s and p50/p99 of
-    bt_search_batch per call, every result checked against numpy's binary
-    search over the keys."""
+    bt_search_batch per call (the device's time: small calls are queued
+    behind a device spin, see _time_calls), every result checked against
+    numpy's binary search over the keys."""
     import torch
 
     def run(t, k, v, B, z, seed, calls):
@@ -646,7 +662,9 @@ def sweep_leg(a, bt, stream, keys, vals, tree):
         return {"lookups_per_s": B / (statistics.fmean(us) / 1e6), "p50_us": us[len(us) // 2],
                 "p99_us": us[min(len(us) - 1, int(0.99 * len(us)))], "correct": ok}
 
-    out = {"batch_sweep": {"workload": f"{keys.size} uniform uint64 keys, fanout {a.fanout}, 90% hits"},
+    out = {"timing": "device time per call: each call queued behind a device spin, so that the host's "
+                     "submission is not timed",
+           "batch_sweep": {"workload": f"{keys.size} uniform uint64 keys, fanout {a.fanout}, 90% hits"},
            "tree_sweep": {"workload": "uniform uint64 keys, fanout 32, batch 1024 uniform queries, 90% hits"}}
     for dist, z in (("uniform", None), ("zipf1.1", 1.1)):
         row = {}
@@ -1237,18 +1255,14 @@ def run_ours(a):
             w1 = torch.empty(max(n1, 1), dtype=torch.uint8, device="cuda")
             for _ in range(20):
                 bt.bt_search_batch(tree.handle, qs, b, v1, f1, w1, n1, stream)
-            ts = []
-            for i in range(500):
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                bt.bt_search_batch(tree.handle, qs, b, v1, f1, w1, n1, stream)
-                e1.record(stream)
-                ts.append((e0, e1))
-            torch.cuda.synchronize()
-            us = sorted(1e3 * x.elapsed_time(y) for x, y in ts)
+            fn = lambda: bt.bt_search_batch(tree.handle, qs, b, v1, f1, w1, n1, stream)
+            us = _time_calls(fn, 500, None, stream)
+            su = _time_calls(fn, 500, None, stream, submit=True)
             lat[f"b{b}"] = {"p50_us": us[len(us) // 2], "p99_us": us[int(0.99 * len(us))],
-                            "lookups_per_s": b / (statistics.fmean(us) / 1e6)}
+                            "lookups_per_s": b / (statistics.fmean(us) / 1e6),
+                            "with_submission": {"p50_us": su[len(su) // 2], "p99_us": su[int(0.99 * len(su))]}}
+        lat["timing"] = ("device time of each call (queued behind a device spin, so that the host's "
+                         "submission is not timed); with_submission: the host's submission included")
         line["small_batch_latency"] = lat
 
     if not a.no_designs:
