@@ -549,6 +549,37 @@ def _learned_case(bt, flush, stream, keys, label):
 
 # ------------------------------------------------------ paper key format leg
 
+def _steps_in_turn(bt, tree, q, B, out, ws, nb, steps: int = 100):
+    """Lookups/s of `steps` searches of one batch issued back to back with
+    nothing flushed between them: on one stream, and with two in flight on
+    two streams (each with its own workspace and outputs, the partition held
+    to one block per SM, as the main loop's two-in-flight steps)."""
+    import torch
+    outs = [out, tree.alloc_outputs(B)]
+    wss = [ws, torch.empty_like(ws)]
+    sts = [torch.cuda.Stream(), torch.cuda.Stream()]
+    res = {}
+    for label, nst, corun in (("one_stream", 1, (0, 0)), ("two_in_flight", 2, (0, 1))):
+        bt.bt_tree_set_corun(tree.handle, *corun)
+        for i in range(4):
+            bt.bt_search_batch(tree.handle, q, B, *outs[i % nst], wss[i % nst], nb, sts[i % nst])
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(sts[0])
+        sts[1].wait_event(e0)
+        for i in range(steps):
+            bt.bt_search_batch(tree.handle, q, B, *outs[i % nst], wss[i % nst], nb, sts[i % nst])
+        sts[0].wait_stream(sts[1])
+        e1.record(sts[0])
+        torch.cuda.synchronize()
+        res[label] = {"lookups_per_s": B * steps / (e0.elapsed_time(e1) / 1e3),
+                      "us_per_batch": 1e3 * e0.elapsed_time(e1) / steps}
+    bt.bt_tree_set_corun(tree.handle, 0, 0)
+    res["note"] = "nothing flushed between steps; two_in_flight: partition at one block per SM"
+    return res
+
+
 def paper_keys_leg(a, bt, flush, stream, peak):
     """The paper's own tree and key format (Sec. V): 2^20 entries of 32-byte
     keys (lexicographic byte order) with 8-byte data, fanout 16; batches of
@@ -585,6 +616,8 @@ def paper_keys_leg(a, bt, flush, stream, peak):
                "correct": bool(np.array_equal(v.cpu().numpy(), want_v) and
                                np.array_equal(f.cpu().numpy(), hit.astype(np.uint8)))}
         if B > 4096:
+            row["l2"] = "flushed before every call"
+            row["steps_in_turn"] = _steps_in_turn(bt, tree, q, B, (v, f), ws, nb)
             # the descent alone on the batch partitioned on log2 B bits, against its
             # algorithmic bytes
             sq = torch.empty_like(q)
