@@ -550,7 +550,12 @@ bt_status bt_check_timeouts(void);
  * through L1 or staged; synchronous with cp.async or bulk-copy staging; two
  * queries per lane); keep the fastest.  *out receives the tree built with
  * the best fanout and launch parameters applied, *best the choice and its
- * time.  Synchronizes `stream`.  Errors: as bt_build, plus BT_ERR_ARG.
+ * time.  A sample with fewer 32-query chunks per SM than a warps-per-block
+ * setting runs the pipelined descent in smaller blocks whatever that setting
+ * is (see bt_tree_set_launch), so such settings are not tried for it and the
+ * pipelined designs keep 8 warps per block: tune on a batch of the size the
+ * tree will serve.  Synchronizes `stream`.  Errors: as bt_build, plus
+ * BT_ERR_ARG.
  * No counterpart in the paper (its fanout is fixed by the key size).
  */
 bt_status bt_autotune(const void *h_keys, const void *h_vals, uint64_t n, bt_width key_w, bt_width val_w,

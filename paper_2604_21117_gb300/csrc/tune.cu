@@ -64,7 +64,9 @@ extern "C" bt_status bt_autotune(const void *h_keys, const void *h_vals, uint64_
     if (!out || !best || !d_sample || nsample == 0 || nsample >= (1ull << 31)) return BT_ERR_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     Scratch sc;
-    const uint64_t ws_bytes = (8 * nsample + 4 * nsample) * 2 + 1024 * 1024 + 256ull * ((nsample + 4095) / 4096) * 4;
+    // a search's workspace for any key width: at most 44 bytes per query
+    // (32-byte keys: keys, positions and pairs) plus alignment and counters
+    const uint64_t ws_bytes = 64 * nsample + 1024 * 1024;
     cudaError_t e = cudaMalloc(&sc.ws, ws_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&sc.vals, nsample * 8);
     if (e == cudaSuccess) e = cudaMalloc(&sc.found, nsample);
@@ -77,6 +79,19 @@ extern "C" bt_status bt_autotune(const void *h_keys, const void *h_vals, uint64_
     const uint32_t fanouts[] = {8, 16, 32, 64};
     const uint32_t warps[] = {4, 8, 16};
     const uint32_t pins[] = {0, 16384, 49152};
+    // The pipelined descent runs a batch with fewer 32-query chunks per SM
+    // than the warps per block in blocks of that many warps (at least two):
+    // a sample that small cannot choose those warps, which then keep the
+    // default (8).
+    int sms = 0;
+    e = btgb::dev_sm_count(&sms);
+    if (e != cudaSuccess) {
+        btgb::set_error_detail("autotune device query", e);
+        return BT_ERR_CUDA;
+    }
+    const uint64_t sample_per_sm = ((nsample + 31) / 32 + static_cast<uint64_t>(sms > 0 ? sms : 1) - 1) /
+                                   static_cast<uint64_t>(sms > 0 ? sms : 1);
+    constexpr uint32_t kDefaultWarps = 8;
     bt_tree *keep = nullptr;
     bt_tune b{0, 0, 0, 0, 1, 0, 0.0f};
     for (uint32_t m : fanouts) {
@@ -100,6 +115,7 @@ extern "C" bt_status bt_autotune(const void *h_keys, const void *h_vals, uint64_
                 static const uint32_t kStage[5] = {BT_STAGE_PIPELINED, BT_STAGE_PIPELINED, BT_STAGE_CP_ASYNC,
                                                    BT_STAGE_BULK, BT_STAGE_CP_ASYNC};
                 const uint32_t sm = kStage[cfg], lq = cfg == 4 ? 2u : 1u, inner = cfg == 1 ? 1u : 0u;
+                if (sm == BT_STAGE_PIPELINED && sample_per_sm < w && w != kDefaultWarps) continue;
                 bt_tree_set_launch(t, w, p);
                 bt_tree_set_staging(t, sm);
                 bt_tree_set_lane_queries(t, lq);

@@ -151,6 +151,9 @@ def test_autotune_returns_a_correct_tree(bt):
     assert best.inner_staged in (0, 1)
     assert best.us_per_batch > 0
     assert tree.fanout == best.fanout
+    # 1024 queries are under one chunk per SM: the pipelined designs keep the default blocks
+    if best.staging == bt.BT_STAGE_PIPELINED:
+        assert best.warps_per_block == 8
     o = OracleTree(keys, vals, best.fanout)
     q = W.make_queries(keys, 30_000, 0.8, seed=67, width_bits=64)
     v, f = tree.search(torch.from_numpy(q).cuda())
