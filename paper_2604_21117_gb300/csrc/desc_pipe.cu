@@ -20,8 +20,12 @@
 //                 issued as bulk copies, one per leaf block, completing on the
 //                 mbarrier while chunk i+1 walks its inner levels.
 //
-// A warp holding more distinct leaves than its slots stages the rest in
-// further rounds, waited for at once.  Learned searches start from the
+// A warp holding more distinct leaves than its slots stages the first
+// slots' worth.  Over a partitioned batch (rarely more than the slots) the
+// rest follow in further rounds, waited for at once; over a batch searched
+// as given (TAIL_L1: up to 32 leaves a chunk) the lanes whose leaf is beyond
+// the slots prefetch its lines into L1 when the copies are issued and rank
+// in it from there, in the same iteration as the staged ones.  Learned searches start from the
 // model's predicted leaf where its window proves the leaf, lane by lane; the
 // other lanes walk the inner levels.  Everything is integer compares.
 #include <cuda_runtime.h>
@@ -152,7 +156,7 @@ __device__ __forceinline__ void leaf_rank_round(const K *stage, int rb, int nu, 
 // MODEL: kModelNone for the plain descent, kModelPL or kModelMLP for the
 // learned one (separate instantiations, so that the MLP's registers do not
 // limit the others).
-template <typename K, typename V, int M, bool COUNT, int MODEL>
+template <typename K, typename V, int M, bool COUNT, int MODEL, bool TAIL_L1 = false>
 __global__ void BT_DESCEND_REGS k_descend(
     const DevTree t, const RawOf<K> *__restrict__ q, const uint32_t *__restrict__ qidx,
     const PartRec<K> *__restrict__ recs, uint64_t nq, V *__restrict__ out_v, uint8_t *__restrict__ out_f,
@@ -396,16 +400,24 @@ __global__ void BT_DESCEND_REGS k_descend(
             int r = 0;
             bool eq = false;
             leaf_rank_round<K, M>(lstage, 0, a_U < SL ? a_U : SL, a_slot, a_key, ballot, lane, r, eq);
-            for (int rb = SL; rb < a_U; rb += SL) {  // further rounds, waited for at once
-                const int nu = (a_U - rb < SL) ? a_U - rb : SL;
-                __syncwarp();
-                issue_leaf_round<K, M>(lstage, lkeys, list + rb, nu, mbar, lane);
-                if (!mbar_wait_warp(mbar, phase, wait_polls)) {
-                    mbar_give_up(mbar, phase, lane);
-                    return;
+            if constexpr (TAIL_L1) {
+                if (a_slot >= SL) {  // a leaf beyond the slots: its lines were prefetched into L1
+                    const K *blk = lkeys + static_cast<uint64_t>(a_node) * M;
+                    r = block_rank_l1<K, M>(blk, a_key);
+                    eq = (ld_key(blk + r) == a_key);
                 }
-                phase ^= 1u;
-                leaf_rank_round<K, M>(lstage, rb, nu, a_slot, a_key, ballot, lane, r, eq);
+            } else {
+                for (int rb = SL; rb < a_U; rb += SL) {  // further rounds, waited for at once
+                    const int nu = (a_U - rb < SL) ? a_U - rb : SL;
+                    __syncwarp();
+                    issue_leaf_round<K, M>(lstage, lkeys, list + rb, nu, mbar, lane);
+                    if (!mbar_wait_warp(mbar, phase, wait_polls)) {
+                        mbar_give_up(mbar, phase, lane);
+                        return;
+                    }
+                    phase ^= 1u;
+                    leaf_rank_round<K, M>(lstage, rb, nu, a_slot, a_key, ballot, lane, r, eq);
+                }
             }
             const uint64_t cnt = t.cbase[LEAF] + (a_node < t.crem[LEAF] ? 1u : 0u);
             const bool hit = (static_cast<uint64_t>(r) < cnt) && eq;
@@ -424,6 +436,14 @@ __global__ void BT_DESCEND_REGS k_descend(
         if (COUNT && lane == 0) atomicAdd(fetch + LEAF, static_cast<unsigned long long>(U));
         __syncwarp();
         issue_leaf_round<K, M>(lstage, lkeys, list, U < SL ? U : SL, mbar, lane);
+        if constexpr (TAIL_L1) {
+            if (slot >= SL) {  // beyond the slots: into L1 now, ranked from there next iteration
+                const unsigned char *b =
+                    reinterpret_cast<const unsigned char *>(lkeys + static_cast<uint64_t>(node) * M);
+#pragma unroll
+                for (int i = 0; i < (BLK + 127) / 128; ++i) prefetch_l1(b + 128 * i);
+            }
+        }
         a_live = true;
         a_valid = valid;
         a_key = key;
@@ -473,7 +493,7 @@ static cudaError_t launch_with_window(void (*kern)(KArgs...), unsigned grid, int
     return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
-template <typename K, typename V, int M, bool COUNT, int MODEL>
+template <typename K, typename V, int M, bool COUNT, int MODEL, bool TAIL_L1 = false>
 static cudaError_t launch_pipe(const DescendArgs &a, cudaStream_t s)
 {
     // inner levels staged (1) or through L1 (0); "auto" (2) stages them for a
@@ -499,7 +519,7 @@ static cudaError_t launch_pipe(const DescendArgs &a, cudaStream_t s)
     const ModelDev &md = a.md ? *a.md : none;
     const int mbytes = LEARN ? static_cast<int>(model_smem_bytes(md)) : 0;
     const int smem = static_cast<int>(t.pin_bytes) + mbytes + nw * pipe_smem_per_warp<K, M, LEARN>(istage);
-    auto kern = k_descend<K, V, M, COUNT, MODEL>;
+    auto kern = k_descend<K, V, M, COUNT, MODEL, TAIL_L1>;
     constexpr int max_model = LEARN ? static_cast<int>(kModelSmemSegments) * 20 : 0;
     e = ensure_dyn_smem(reinterpret_cast<const void *>(kern),
                         kPinBudgetMax + max_model + kDescWarpsMax * pipe_smem_per_warp<K, M, LEARN>(true));
@@ -523,6 +543,8 @@ static cudaError_t pipe_mode(const DescendArgs &a, cudaStream_t s)
         }
     }
     if (a.fetch) return launch_pipe<K, V, M, true, kModelNone>(a, s);
+    // a batch searched as given: chunks meet up to 32 leaves, more than the slots
+    if (!a.recs && !a.qidx) return launch_pipe<K, V, M, false, kModelNone, true>(a, s);
     return launch_pipe<K, V, M, false, kModelNone>(a, s);
 }
 
