@@ -222,9 +222,8 @@ __global__ void BT_DESCEND_REGS k_descend(
             }
         }
     }
-    cp_async_wait_all();
-    __syncthreads();
-    // the batch (and the outputs) belong to the previous kernel until it is done
+    // the batch (and the outputs) belong to the previous kernel until it is
+    // done; the copies above stay in flight meanwhile
     pdl_wait();
 
     const uint64_t nchunks = (nq + 31) / 32;
@@ -244,6 +243,10 @@ __global__ void BT_DESCEND_REGS k_descend(
         load_query<K>(q, qidx, recs, v ? pos : c * 32, key_n, dst_n);
         if (!v) dst_n = 0;
     }
+    // the pinned levels and the model, copied above (the first queries'
+    // loads overlap the copies)
+    cp_async_wait_all();
+    __syncthreads();
     // Chunk A: its leaf round 0 is in flight.
     bool a_live = false, a_valid = false;
     K a_key = key_n;
