@@ -22,10 +22,11 @@
 //
 // A warp holding more distinct leaves than its slots stages the first
 // slots' worth.  Over a partitioned batch (rarely more than the slots) the
-// rest follow in further rounds, waited for at once; over a batch searched
-// as given (TAIL_L1: up to 32 leaves a chunk) the lanes whose leaf is beyond
-// the slots prefetch its lines into L1 when the copies are issued and rank
-// in it from there, in the same iteration as the staged ones.  Learned searches start from the
+// rest follow in further rounds, waited for at once; over a small batch
+// searched as given (TAIL_L1: up to 32 leaves a chunk, at most 16 chunks per
+// SM) the lanes whose leaf is beyond the slots prefetch its lines into L1
+// when the copies are issued and rank in it from there, in the same
+// iteration as the staged ones.  Learned searches start from the
 // model's predicted leaf where its window proves the leaf, lane by lane; the
 // other lanes walk the inner levels.  Everything is integer compares.
 #include <cuda_runtime.h>
@@ -546,8 +547,16 @@ static cudaError_t pipe_mode(const DescendArgs &a, cudaStream_t s)
         }
     }
     if (a.fetch) return launch_pipe<K, V, M, true, kModelNone>(a, s);
-    // a batch searched as given: chunks meet up to 32 leaves, more than the slots
-    if (!a.recs && !a.qidx) return launch_pipe<K, V, M, false, kModelNone, true>(a, s);
+    // A small batch searched as given: its chunks meet up to 32 leaves, more
+    // than the slots, and rank the rest through L1.  From about 16 chunks per
+    // SM the prefetched lines no longer stay in L1 until they are read (at
+    // 2^20 queries on a 10^6-key tree: 67 us against 61 with the further
+    // rounds), so larger batches keep the rounds.
+    int sms = 0;
+    const cudaError_t e = dev_sm_count(&sms);
+    if (e != cudaSuccess) return e;
+    if (!a.recs && !a.qidx && (a.nq + 31) / 32 <= 16ull * static_cast<uint64_t>(sms > 0 ? sms : 1))
+        return launch_pipe<K, V, M, false, kModelNone, true>(a, s);
     return launch_pipe<K, V, M, false, kModelNone>(a, s);
 }
 
