@@ -383,7 +383,7 @@ typedef struct bt_forest_tune {
     uint32_t lane_queries;    /* 0: each tree's own, 1 or 2: that many queries per lane for all trees */
     uint32_t staging;         /* 0: each tree's own design, 1: all read through L1, 2: all staged per warp */
     uint32_t pin_applied;     /* out: bytes of pinned levels the budget admitted */
-    float us;                 /* out (bt_forest_autotune): median time of the work list */
+    float us;                 /* out (bt_forest_autotune): device time per call of the work list */
 } bt_forest_tune;
 
 /* Replace a forest's launch settings (synchronizes the device; CUDA graphs
@@ -424,9 +424,10 @@ bt_status bt_forest_search(const bt_forest *forest, const bt_batch_desc *d_batch
  * bt_forest_autotune -- time the work list (arguments as bt_forest_search)
  * under every combination of warps per block {4, 8, 16}, pin budget
  * {0, 16384, 49152, 98304}, queries per lane {each tree's, 1, 2} and
- * staging {each tree's, all through L1, all staged}; keep the fastest (median
- * of 5 timed runs after 2 untimed, CUDA events on `stream`) as the forest's
- * settings and return it in *best.  Synchronizes the device.  No counterpart
+ * staging {each tree's, all through L1, all staged}; keep the fastest (after 2
+ * untimed calls, 3 runs of 5 calls issued back to back behind a short device
+ * spin, timed together with CUDA events on `stream`; the median per call) as
+ * the forest's settings and return it in *best.  Synchronizes the device.  No counterpart
  * in the paper (its kernel's shape is fixed by the FPGA build).
  * Errors: as bt_forest_search.
  */
@@ -448,7 +449,8 @@ typedef struct bt_tune {
     uint32_t staging;         /* BT_STAGE_PIPELINED, BT_STAGE_CP_ASYNC or BT_STAGE_BULK */
     uint32_t lane_queries;    /* queries per lane of the descent: 1 or 2 */
     uint32_t inner_staged;    /* pipelined descent: inner levels staged (1) or read through L1 (0) */
-    float us_per_batch;       /* median time of the sample batch with these settings */
+    float us_per_batch;       /* device time per call of the sample batch with these settings (10 calls
+                               * issued back to back, median of 5 runs) */
 } bt_tune;
 
 /* Set the descent launch parameters of a built tree (not thread-safe with

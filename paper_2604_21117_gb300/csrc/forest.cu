@@ -636,6 +636,15 @@ extern "C" bt_status bt_forest_get_launch(const bt_forest *f, bt_forest_tune *ou
     return BT_OK;
 }
 
+// Keeps the stream busy for a fixed number of clock cycles (the autotuner's
+// timed calls queue behind it).
+static __global__ void k_tune_spin(long long cycles)
+{
+    const long long t0 = clock64();
+    while (clock64() - t0 < cycles) {
+    }
+}
+
 // The work list, queries and values are aligned to their element sizes.
 static bool forest_arrays_aligned(const bt_forest *f, const void *d_batches, const void *q, const void *v)
 {
@@ -692,22 +701,33 @@ extern "C" bt_status bt_forest_autotune(bt_forest *f, const bt_batch_desc *d_bat
                         cudaEventDestroy(e1);
                         return st;
                     }
+                    // two warm-up calls, then kReps runs of kCalls calls issued
+                    // behind a spin of about 100 us (so that they run back to
+                    // back on the device), timed together; median per call
+                    constexpr int kCalls = 5, kReps = 3;
                     std::vector<float> ms;
-                    for (int r = 0; r < 7 && e == cudaSuccess; ++r) {
-                        if (r >= 2) e = cudaEventRecord(e0, s);
-                        st = bt_forest_search(f, d_batches, nbatches, d_queries, nq, d_out_vals, d_out_found,
-                                              d_workspace, ws_bytes, 0, stream);
-                        if (st != BT_OK) {
-                            cudaEventDestroy(e0);
-                            cudaEventDestroy(e1);
-                            return st;
+                    for (int r = 0; r < 2 + kReps && e == cudaSuccess; ++r) {
+                        const bool timed = r >= 2;
+                        if (timed) {
+                            k_tune_spin<<<1, 32, 0, s>>>(200000);
+                            e = cudaGetLastError();
+                            if (e == cudaSuccess) e = cudaEventRecord(e0, s);
                         }
-                        if (r >= 2) {
+                        for (int i = 0; i < (timed ? kCalls : 1) && e == cudaSuccess; ++i) {
+                            st = bt_forest_search(f, d_batches, nbatches, d_queries, nq, d_out_vals, d_out_found,
+                                                  d_workspace, ws_bytes, 0, stream);
+                            if (st != BT_OK) {
+                                cudaEventDestroy(e0);
+                                cudaEventDestroy(e1);
+                                return st;
+                            }
+                        }
+                        if (timed) {
                             if (e == cudaSuccess) e = cudaEventRecord(e1, s);
                             if (e == cudaSuccess) e = cudaEventSynchronize(e1);
                             float x = 0;
                             if (e == cudaSuccess) e = cudaEventElapsedTime(&x, e0, e1);
-                            ms.push_back(x);
+                            ms.push_back(x / kCalls);
                         }
                     }
                     if (e != cudaSuccess) break;

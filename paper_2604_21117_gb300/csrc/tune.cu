@@ -29,9 +29,25 @@ struct Scratch {
     }
 };
 
+// Keeps the stream busy for a fixed number of clock cycles, so that the
+// calls queued behind it run back to back on the device however slowly the
+// host submits them.
+__global__ void k_spin(long long cycles)
+{
+    const long long t0 = clock64();
+    while (clock64() - t0 < cycles) {
+    }
+}
+
+// Device time per call of the sample: kCalls calls issued behind a spin of
+// about 100 us and timed together, median of kReps such runs.  (Single calls
+// would time the host's submission too, and the event timer moves in steps
+// of about 2 us.)
 bt_status time_search(const bt_tree *t, const void *d_sample, uint64_t nq, Scratch &sc, uint64_t ws_bytes,
                       cudaStream_t s, float *us)
 {
+    constexpr int kCalls = 10, kReps = 5;
+    constexpr long long kSpinCycles = 200000;
     const bt_stream bs = reinterpret_cast<bt_stream>(s);
     for (int i = 0; i < 2; ++i) {
         const bt_status st = bt_search_batch(t, d_sample, nq, sc.vals, static_cast<uint8_t *>(sc.found), sc.ws,
@@ -39,16 +55,20 @@ bt_status time_search(const bt_tree *t, const void *d_sample, uint64_t nq, Scrat
         if (st != BT_OK) return st;
     }
     std::vector<float> ms;
-    for (int i = 0; i < 7; ++i) {
+    for (int rep = 0; rep < kReps; ++rep) {
+        k_spin<<<1, 32, 0, s>>>(kSpinCycles);
+        if (cudaGetLastError() != cudaSuccess) return BT_ERR_CUDA;
         cudaEventRecord(sc.e0, s);
-        const bt_status st = bt_search_batch(t, d_sample, nq, sc.vals, static_cast<uint8_t *>(sc.found), sc.ws,
-                                             ws_bytes, bs);
-        if (st != BT_OK) return st;
+        for (int i = 0; i < kCalls; ++i) {
+            const bt_status st = bt_search_batch(t, d_sample, nq, sc.vals, static_cast<uint8_t *>(sc.found), sc.ws,
+                                                 ws_bytes, bs);
+            if (st != BT_OK) return st;
+        }
         cudaEventRecord(sc.e1, s);
         if (cudaEventSynchronize(sc.e1) != cudaSuccess) return BT_ERR_CUDA;
         float x = 0;
         cudaEventElapsedTime(&x, sc.e0, sc.e1);
-        ms.push_back(x);
+        ms.push_back(x / kCalls);
     }
     std::sort(ms.begin(), ms.end());
     *us = 1000.0f * ms[ms.size() / 2];
