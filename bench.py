@@ -48,7 +48,7 @@ L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) of one k_descend launch on the default workload,
 # from one ncu capture of it (summarised under profiles/); valid only while
 # the descent's source (desc_pipe.cu and descent.cuh) hashes to the same value.
-NCU_DESCEND_TRAFFIC = {"descend_src_sha256": "a87327b35e88bded", "bytes_per_launch": 223306240}
+NCU_DESCEND_TRAFFIC = {"descend_src_sha256": "9f8dc9871dc2dfda", "bytes_per_launch": 223253760}
 
 
 def parse_args(argv=None):

@@ -540,13 +540,6 @@ static cudaError_t launch_pipe(const DescendArgs &a, cudaStream_t s)
 template <typename K, typename V, int M>
 static cudaError_t pipe_mode(const DescendArgs &a, cudaStream_t s)
 {
-    if constexpr (!std::is_same<K, Key32>::value) {
-        if (a.md) {
-            if (a.md->kind == kModelPL) return launch_pipe<K, V, M, false, kModelPL>(a, s);
-            return launch_pipe<K, V, M, false, kModelMLP>(a, s);
-        }
-    }
-    if (a.fetch) return launch_pipe<K, V, M, true, kModelNone>(a, s);
     // A small batch searched as given: its chunks meet up to 32 leaves, more
     // than the slots, and rank the rest through L1.  From about 16 chunks per
     // SM the prefetched lines no longer stay in L1 until they are read (at
@@ -555,8 +548,20 @@ static cudaError_t pipe_mode(const DescendArgs &a, cudaStream_t s)
     int sms = 0;
     const cudaError_t e = dev_sm_count(&sms);
     if (e != cudaSuccess) return e;
-    if (!a.recs && !a.qidx && (a.nq + 31) / 32 <= 16ull * static_cast<uint64_t>(sms > 0 ? sms : 1))
-        return launch_pipe<K, V, M, false, kModelNone, true>(a, s);
+    const bool tail_l1 =
+        !a.recs && !a.qidx && (a.nq + 31) / 32 <= 16ull * static_cast<uint64_t>(sms > 0 ? sms : 1);
+    if constexpr (!std::is_same<K, Key32>::value) {
+        if (a.md) {
+            // PL windows on skewed keys span many leaves read through L1, and
+            // the L1 path for the leaves cost them a step at batch 1024 (12.3
+            // -> 14.3 us on lognormal keys); the MLP's gained (22.5 -> 18.4 us)
+            if (a.md->kind == kModelPL) return launch_pipe<K, V, M, false, kModelPL>(a, s);
+            return tail_l1 ? launch_pipe<K, V, M, false, kModelMLP, true>(a, s)
+                           : launch_pipe<K, V, M, false, kModelMLP>(a, s);
+        }
+    }
+    if (a.fetch) return launch_pipe<K, V, M, true, kModelNone>(a, s);
+    if (tail_l1) return launch_pipe<K, V, M, false, kModelNone, true>(a, s);
     return launch_pipe<K, V, M, false, kModelNone>(a, s);
 }
 
